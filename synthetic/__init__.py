@@ -1,0 +1,70 @@
+"""Seeded synthetic inputs shared by the oracle-side tests and the GPU path.
+
+This module holds workload descriptions (mesh sizes, orders, material
+constants, boundary faces, step sizes, seeds) and seeded random number draws
+only.  It contains none of the method's arithmetic: no basis, quadrature,
+material law or solver.  Both the oracle and the product turn these plain
+numbers into their own data structures independently.
+
+Workloads follow the paper's test shapes (Sec. 5: unit cubes of hexahedra,
+neo-Hookean E = 1000, nu = 0.3, rho = 1; bases ST/nodal/SDME with k = 0.5 and
+lambda = 100) scaled to the GPU problem sizes:
+
+* ``cube_p4``   unit cube, 4x4x4 hexes, P = 4; bottom face clamped, uniform
+                dead top traction ramped over 10 implicit Newmark steps.
+* ``beam_p8``   [0,8]x[0,1]x[0,1] cantilever, 64x8x8 hexes, P = 8, nu = 0.45;
+                x = 0 clamped, dead shear traction on x = 8 ramped over 20 steps.
+* ``static_fab``  the paper's static fabricated problem (Sec. 5.1): unit cube,
+                2x2x2 hexes, x = 0 clamped.
+
+Load magnitudes are produced by ``tests/golden/make_golden.py`` (which calls
+only the oracle) and stored in ``tests/golden/loads.json``.
+"""
+import json
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LOADS = os.path.join(os.path.dirname(_HERE), "tests", "golden", "loads.json")
+
+WORKLOADS = {
+    "cube_p4": dict(
+        elems=(4, 4, 4), P=4, lengths=(1.0, 1.0, 1.0), E=1.0e3, nu=0.3, rho=1.0,
+        clamp={"zmin": (0, 1, 2)}, traction_face="zmax", traction_dir=(0.0, 0.0, -1.0),
+        steps=10, dt=0.01, newton_tol=1e-8, pcg_rtol=1e-10, k=0.5, lam=100.0,
+        load_key="cube_p4_traction"),
+    "beam_p8": dict(
+        elems=(64, 8, 8), P=8, lengths=(8.0, 1.0, 1.0), E=1.0e3, nu=0.45, rho=1.0,
+        clamp={"xmin": (0, 1, 2)}, traction_face="xmax", traction_dir=(0.0, 0.0, -1.0),
+        steps=20, dt=1.0, newton_tol=1e-8, pcg_rtol=1e-10, k=0.5, lam=100.0,
+        load_key="beam_traction"),
+    "static_fab": dict(
+        elems=(2, 2, 2), P=4, lengths=(1.0, 1.0, 1.0), E=1.0e3, nu=0.3, rho=1.0,
+        clamp={"xmin": (0, 1, 2)}, k=0.5, lam=100.0),
+}
+
+
+def workload(name, **overrides):
+    w = dict(WORKLOADS[name])
+    w.update(overrides)
+    return w
+
+
+def load_magnitude(key):
+    """Traction magnitude stored by the golden script (oracle calibration)."""
+    with open(_LOADS) as f:
+        return float(json.load(f)[key]["value"])
+
+
+def rng(seed):
+    return np.random.default_rng(seed)
+
+
+def random_vector(n, seed, scale=1.0):
+    """n standard-normal draws times ``scale`` (float64)."""
+    return rng(seed).standard_normal(n) * scale
+
+
+def random_uniform(n, seed, lo=-1.0, hi=1.0):
+    return rng(seed).uniform(lo, hi, n)
