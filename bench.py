@@ -1,0 +1,334 @@
+"""Benchmark: matrix-free neo-Hookean tangent matvecs inside Newton + Jacobi-PCG
+implicit Newmark steps on the 64x8x8-hex, P = 8 cantilever (6.50 M DOFs).
+
+One step = one implicit Newmark step of the load ramp (Newton iterations with
+a float64 residual, each solved by Jacobi-PCG whose iterations run the
+tangent matvec), i.e. one pass of the whole hot path.  Inputs are synthetic
+(seeded workload ``beam_p8``: E = 1000, nu = 0.45, dead tip shear traction
+calibrated by the oracle), resident in HBM; every working vector and the
+per-Gauss-point state exceed the 129 MB L2, so no flush is needed.
+
+    python bench.py [--steps K] [--warmup W] [--precision mixed|fp64] [--basis sdme_h]
+    python bench.py --impl reference      # the FP64 CPU oracle on host cores
+
+Prints one JSON line (rank 0).  Multi-GPU: independent replicas (the single
+mesh is not sharded), launched one rank per GPU by torchrun.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synthetic import load_magnitude, workload  # noqa: E402
+
+METRIC = ("tangent-matvec DOF/s and Newton-PCG time per implicit step, SDME vs nodal, FP64 vs mixed at 1e-8")
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+FP64_PEAK_TFLOPS = 1.25                               # GB300 FP64 rate (profiling recipe table)
+
+
+def lame(E, nu):
+    return E / (2.0 * (1.0 + nu)), E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+
+
+def tangent_flops_per_element(P):
+    """Algorithmic float ops of one element's tangent action, as the kernel
+    computes it: 3 components x (interpolation n^3Q + n^2Q^2 + nQ^3 +
+    collocated derivatives 3 Q^4) multiply-adds, forward and transposed, plus
+    207 flops of pointwise linearised stress per Gauss point."""
+    n, Q = P + 1, P + 2
+    mac = 3 * (n ** 3 * Q + n ** 2 * Q ** 2 + n * Q ** 3 + 3 * Q ** 4)
+    return 2 * 2 * mac + 207 * Q ** 3
+
+
+def tangent_bytes(P, nelem, ndof, word_state, word_vec):
+    """Algorithmic DRAM bytes of one tangent launch: the per-Gauss-point
+    state (10 words), x read once, y read and written once."""
+    Q = P + 2
+    return 10 * Q ** 3 * nelem * word_state + 3 * ndof * word_vec
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_matvec(w, basis, nsample, seed=0):
+    """The FP64 oracle's tangent action on a bounded sample of elements of
+    the same mesh; returns (DOF/s scaled to the whole mesh, seconds, cores)."""
+    from oracle.assembly import Discretization
+    from oracle.basis1d import Basis1D
+    from oracle.hexmesh import BoxMesh
+    from oracle.material import lame as olame
+    from synthetic import random_vector
+    mu, lam = olame(w["E"], w["nu"])
+    mesh = BoxMesh(*w["elems"], w["P"], w["lengths"])
+    for f, comps in w["clamp"].items():
+        mesh.clamp(f, comps)
+    d = Discretization(mesh, Basis1D(w["P"], basis), mu, lam, w["rho"])
+    u = random_vector(mesh.ndof, seed + 1, 1e-4)
+    x = random_vector(mesh.ndof, seed + 2)
+    els = np.arange(min(nsample, mesh.nelem))
+    t0 = time.perf_counter()
+    for s in range(0, len(els), 64):
+        e = els[s:s + 64]
+        Ue, Xe = d.gather(u, e), d.gather(x, e)
+        Ye = d.ref.tangent_action(Ue, Xe, mu, lam) + 4.0 * d.ref.mass_action(Xe, w["rho"])
+        d.scatter(Ye, e)
+    dt = time.perf_counter() - t0
+    dofs_per_s = mesh.ndof * (len(els) / mesh.nelem) / dt
+    return dofs_per_s, dt, os.cpu_count()
+
+
+def run_reference(args, w):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    per_step = []
+    sample = args.ref_sample
+    for i in range(args.warmup + args.steps):
+        v, dt, cores = cpu_oracle_matvec(w, args.basis, sample, seed=i)
+        if i >= args.warmup:
+            per_step.append((v, dt))
+    value = float(np.mean([v for v, _ in per_step]))
+    ms = float(np.mean([dt for _, dt in per_step]) * 1e3)
+    desc = "FP64 numpy oracle tangent action on %d of %d elements per step, scaled to the mesh" % (
+        sample, int(np.prod(w["elems"])))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "beam_p8: 64x8x8 hexes, P=8, 6502275 DOFs, basis %s" % args.basis},
+            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, w):
+    import torch
+    import paper_2104_13466_gb300 as sd
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = sd.MIXED_FP32 if args.precision == "mixed" else sd.FP64
+    mu, lam = lame(w["E"], w["nu"])
+    ctx = sd.Context(w["elems"], w["lengths"], w["clamp"], mu, lam, w["rho"], w["P"], args.basis, precision=prec)
+    n = ctx.ndof
+    dev = torch.device("cuda", local)
+    unit = torch.zeros(n, dtype=torch.float64, device=dev)
+    t = np.array(w["traction_dir"]) * 1.0
+    ctx.traction_load(w["traction_face"], t, unit)
+    smag = load_magnitude(w["load_key"])
+    u = torch.zeros(n, dtype=torch.float64, device=dev)
+    v = torch.zeros_like(u)
+    a = torch.zeros_like(u)
+    Pn = torch.zeros_like(u)
+    opts = dict(newton_tol=w["newton_tol"], pcg_rtol=w["pcg_rtol"], mixed_rtol=args.mixed_rtol,
+                pcg_maxit=args.pcg_maxit, max_newton=args.max_newton)
+    nsteps = w["steps"]
+    dt = w["dt"]
+    step_i = [0]
+
+    def one_step():
+        step_i[0] += 1
+        k = min(step_i[0], nsteps)
+        torch.mul(unit, smag * k / nsteps, out=Pn)
+        return ctx.implicit_newmark_step(u, v, a, dt, Pn, allow=(sd.NEWTON_DIVERGED, sd.PCG_MAXIT), **opts)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ctx.set_timing(True)
+    t0 = ctx.timing()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            stats.append(one_step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ctx.set_timing(False)
+    t1 = ctx.timing()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    matvecs = sum(s["matvecs"] for s in stats)
+    value = ws * n * matvecs / (ms * 1e-3)
+    tan_ms = (t1["tangent_ms"] - t0["tangent_ms"])
+    tan_launches = t1["tangent_launches"] - t0["tangent_launches"]
+    avg_tan = tan_ms / max(1, tan_launches)
+    wstate = 4 if prec == sd.MIXED_FP32 else 8
+    flops = tangent_flops_per_element(w["P"]) * ctx.nelem
+    nbytes = tangent_bytes(w["P"], ctx.nelem, n, wstate, wstate)
+    achieved_tf = flops / (avg_tan * 1e-3) / 1e12
+    alu_peak = FP32_PEAK_TFLOPS if prec == sd.MIXED_FP32 else FP64_PEAK_TFLOPS
+    hbm_peak, hbm_src = _peaks()
+    achieved_gbs = nbytes / (avg_tan * 1e-3) / 1e9
+
+    # end to end through the public API: host state and load in, host state out
+    pin = [torch.zeros(n, dtype=torch.float64).pin_memory() for _ in range(4)]
+    for p_, d_ in zip(pin, (u, v, a, unit)):
+        p_.copy_(d_)
+    out = [torch.zeros(n, dtype=torch.float64).pin_memory() for _ in range(3)]
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_mv = 0
+    e2.record(stream)
+    for _ in range(args.e2e_steps):
+        for p_, d_ in zip(pin, (u, v, a, unit)):
+            d_.copy_(p_, non_blocking=True)
+        e2e_mv += one_step()["matvecs"]
+        for o_, d_ in zip(out, (u, v, a)):
+            o_.copy_(d_, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e2.elapsed_time(e3)
+    e2e_value = ws * n * e2e_mv / (e2e_ms * 1e-3) if e2e_ms > 0 else None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cv, cdt, cores = cpu_oracle_matvec(w, args.basis, args.ref_sample)
+        cpu = {"value": cv, "unit": "DOF/s", "cores": cores, "kind": "oracle",
+               "sample": "FP64 numpy oracle tangent action on %d of %d elements (%.1f s), scaled to the mesh"
+                         % (args.ref_sample, ctx.nelem, cdt)}
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32-matvec/f64-residual" if prec == sd.MIXED_FP32 else "f64",
+            "data": "synthetic",
+            "config": {"workload": "beam_p8: [0,8]x[0,1]^2 cantilever, 64x8x8 hexes, P=8, %d DOFs, basis %s, "
+                                   "%s, Newton tol %g, dt %g" % (n, args.basis, args.precision, w["newton_tol"], dt),
+                       "global_batch": 1, "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (vectors 52 MB each, Gauss-point state %d MB)"
+                             % (10 * (w["P"] + 2) ** 3 * ctx.nelem * wstate // 2 ** 20)},
+            "newton_pcg_ms_per_step": ms / args.steps,
+            "steps_detail": [{k: s[k] for k in ("newton_iters", "pcg_iters_total", "converged")} for s in stats],
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved_tf / alu_peak, "traffic": None,
+                         "kernel": "tangent_kernel<8,%s>" % ("float,float" if prec == sd.MIXED_FP32 else "double,double"),
+                         "avg_launch_ms": avg_tan, "launches": tan_launches,
+                         "flops_per_launch": flops, "peak_src": "derived from recipe unit counts and max clock",
+                         "hbm_view": {"bytes_per_launch": nbytes, "achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak,
+                                      "frac": achieved_gbs / hbm_peak, "peak_src": hbm_src}},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "DOF/s", "steps": args.e2e_steps,
+                    "h2d_bytes_per_step": 4 * n * 8, "d2h_bytes_per_step": 3 * n * 8},
+            "gpu_launches": int(t1["kernel_launches"] - t0["kernel_launches"]),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--basis", default="sdme_h", choices=["nodal", "modal", "sdme_m", "sdme_k", "sdme_h"])
+    ap.add_argument("--workload", default="beam_p8")
+    ap.add_argument("--mixed-rtol", type=float, default=1e-4)
+    ap.add_argument("--pcg-maxit", type=int, default=20000)
+    ap.add_argument("--max-newton", type=int, default=30)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--ref-sample", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * sdme.h - C ABI of the GB300 matrix-free SDME / neo-Hookean Newton-PCG engine.
+ *
+ * Method: Dias, Suzuki, Valente, Bittencourt, "Simulation of non-linear
+ * structural elastodynamic and impact problems using minimum energy and
+ * simultaneous diagonalization high-order bases" (arXiv:2104.13466).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Mesh.  A box [0,Lx]x[0,Ly]x[0,Lz] split into nx x ny x nz equal hexahedra of
+ *   order P (1 <= P <= 8), all with the same orientation.  The (P+1)^3
+ *   coefficients of each element live on a global lattice of
+ *   Nx x Ny x Nz = (nx P + 1) x (ny P + 1) x (nz P + 1) points; the 1D
+ *   functions are ordered [vertex at -1, internal modes, vertex at +1].
+ * Vectors.  Every global vector is float64, component-major
+ *   ("structure of arrays"): index c*Nn + (iz*Ny + iy)*Nx + ix, c = 0,1,2,
+ *   Nn = Nx*Ny*Nz, length ndof = 3*Nn.  Vector arguments named *_dev are
+ *   device pointers (cudaMalloc'd or torch CUDA tensors) owned by the caller;
+ *   they must not alias each other unless stated.
+ * Streams.  All device work of a context is issued on the stream given to
+ *   sdme_create.  Calls that return host scalars or check the device error
+ *   word synchronise that stream; the others are stream-ordered.
+ * Errors.  Every call returns an sdme_status; nothing throws or traps.  A
+ *   sticky device error word (non-positive Jacobian) is checked at every
+ *   host synchronisation and reported as SDME_NONPOSITIVE_J.
+ * Dirichlet.  Homogeneous or prescribed values on whole box faces, per
+ *   component (clamp[face] bit c).  A DOF is constrained when its lattice
+ *   point lies on a clamped face: every 1D function except the vertex one
+ *   vanishes there.
+ */
+#ifndef SDME_H
+#define SDME_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SDME_OK = 0,
+  SDME_EINVAL = 1,            /* bad argument */
+  SDME_ENOMEM = 2,            /* device or host allocation failed */
+  SDME_ECUDA = 3,             /* a CUDA runtime call failed */
+  SDME_PCG_MAXIT = 4,         /* PCG reached maxit before rtol */
+  SDME_NEWTON_DIVERGED = 5,   /* Newton reached max_newton before tol */
+  SDME_NONPOSITIVE_J = 6,     /* det F <= 0 at some Gauss point */
+  SDME_NAN = 7,               /* non-finite residual or PCG scalar */
+  SDME_TIMEOUT = 8,           /* a bounded device-side wait gave up */
+  SDME_EUNSUPPORTED = 9       /* order or option not built */
+} sdme_status;
+
+/* 1D expansion bases of Sec. 2. */
+typedef enum {
+  SDME_NODAL = 0,    /* Lagrange on GLL points, eqs. lagrangian / shape_functions_lag */
+  SDME_MODAL = 1,    /* Jacobi modal ST basis, eq. BasePadrao1D */
+  SDME_SDME_M = 2,   /* SD internal modes + ME vertex modes, L2 norm (eq. alphaMassa) */
+  SDME_SDME_K = 3,   /* SD + ME, energy norm (eq. alphaRigidez) */
+  SDME_SDME_H = 4    /* SD + ME, Helmholtz norm K + lambda M (eq. alphaKN) */
+} sdme_basis_kind;
+
+typedef enum {
+  SDME_FP64 = 0,      /* everything in float64 */
+  SDME_MIXED_FP32 = 1 /* tangent matvec, diagonal and PCG vectors in float32;
+                         Newton residual, dot-product reductions, PCG scalars
+                         and time-integrator state in float64 */
+} sdme_precision;
+
+enum { SDME_XMIN = 0, SDME_XMAX = 1, SDME_YMIN = 2, SDME_YMAX = 3, SDME_ZMIN = 4, SDME_ZMAX = 5 };
+
+typedef struct {
+  int P;                 /* polynomial order, 1..8 */
+  sdme_basis_kind kind;
+  double k;              /* SD parameter of eq. Y, in [0, 1] (paper: 0.5) */
+  double lambda;         /* Helmholtz parameter of eq. EffectiveStiffness_lambda (paper: 100) */
+  int start_nodal;       /* SDME kinds: build from the Lagrange (1) or Jacobi (0) basis */
+  double jacobi_alpha;   /* modal weights of eq. BasePadrao1D (paper: 1, 1) */
+  double jacobi_beta;
+} sdme_basis_desc;
+
+typedef struct {
+  int nelem[3];          /* hexahedra per direction */
+  double length[3];      /* box edge lengths */
+  unsigned clamp[6];     /* per face (SDME_XMIN..SDME_ZMAX): bit c set = component c constrained */
+} sdme_mesh_desc;
+
+typedef struct {
+  double mu, lambda;     /* Lame parameters of eq. hyperelastic strain energy */
+  double rho;            /* reference density */
+} sdme_material;
+
+typedef struct {
+  double beta, gamma;    /* Newmark parameters (reading of the garbled table: 0.25, 0.5) */
+  double newton_tol;     /* stop when ||psi_k|| <= tol * max(||psi_0||, 1e-14 ||P||) */
+  int max_newton;
+  double pcg_rtol;       /* FP64: ||r|| <= rtol ||b|| */
+  double mixed_rtol;     /* MIXED_FP32: inner PCG tolerance (inexact Newton) */
+  int pcg_maxit;
+} sdme_newton_opts;
+
+typedef struct {
+  int newton_iters;
+  int pcg_iters_total;
+  int matvecs;                 /* tangent matvecs issued */
+  int converged;               /* 1 if the Newton test was met */
+  double residual0;            /* ||psi_0|| */
+  double residual_final;       /* ||psi|| at exit */
+  int pcg_iters[32];           /* per Newton iteration (first 32) */
+  double residuals[33];        /* ||psi_k||, k = 0..min(newton_iters, 32) */
+} sdme_step_stats;
+
+typedef struct {
+  double* u;             /* displacement u_n (in) -> u_{n+1} (out), device */
+  double* v;             /* velocity, device */
+  double* a;             /* acceleration, device */
+} sdme_state;
+
+typedef struct sdme_ctx sdme_ctx;
+
+/* Human-readable name of a status code (static storage). */
+const char* sdme_status_string(sdme_status s);
+
+/*
+ * Host-only.  Build the 1D basis of Sec. 2 and tabulate it at Q Gauss-Legendre
+ * points (Q >= 1; the device path uses Q = P + 2).  Steps: standard basis
+ * (eq. shape_functions_lag or BasePadrao1D), 1D mass/stiffness (eqs.
+ * Matrizesmassa, Matrizesrigidez), partition (eq. BlocosMassa), simultaneous
+ * diagonalisation of the internal block (eqs. diagMassa, L, diagL, Y; each
+ * internal function signed so that its derivative at -1 is positive and
+ * ordered by ascending eigenvalue), minimum-energy vertex modes (eqs.
+ * ExtensaoMEmassa, alphaMassa, alphaRigidez, alphaKN).
+ * Outputs (caller-owned host arrays; any may be NULL), lattice order:
+ *   xq[Q], wq[Q]          Gauss-Legendre points and weights on [-1, 1]
+ *   B[Q*(P+1)]            B[q*(P+1)+j] = phi_j(xq[q])
+ *   D[Q*(P+1)]            D[q*(P+1)+j] = phi_j'(xq[q])
+ *   M1[(P+1)^2], K1[...]  1D mass and stiffness of the final basis
+ * Returns SDME_EINVAL for P outside 1..8, Q outside 1..16 or a bad kind.
+ */
+sdme_status sdme_build_basis1d(const sdme_basis_desc* basis, int Q, double* xq, double* wq,
+                               double* B, double* D, double* M1, double* K1);
+
+/*
+ * Create a context: builds the basis, uploads its tables, allocates device
+ * work buffers (per-Gauss-point linearisation state, PCG vectors).  stream:
+ * the cudaStream_t all of the context's work is issued on; NULL selects the
+ * legacy default stream.  The stream is not owned and must outlive the
+ * context.  Returns SDME_EINVAL for bad sizes/material/basis, SDME_ENOMEM
+ * when a buffer cannot be allocated (nothing is leaked).
+ */
+sdme_status sdme_create(sdme_ctx** out, const sdme_mesh_desc* mesh, const sdme_material* mat,
+                        const sdme_basis_desc* basis, sdme_precision prec, void* stream);
+
+sdme_status sdme_destroy(sdme_ctx* ctx);
+
+/* Sizes: ndof = 3*Nn, lattice dims N[3], element count. */
+sdme_status sdme_get_sizes(const sdme_ctx* ctx, int64_t* ndof, int N[3], int64_t* nelem);
+
+/*
+ * R_dev = R(u), the internal force vector of eq. material virtual work
+ * (second term, S : dE = P : grad du with P = F S of eq. second
+ * Piolla_Kirchhoff relation), for every DOF (no Dirichlet treatment).
+ * Also stores the linearisation state at u.  Always float64.
+ */
+sdme_status sdme_internal_force(sdme_ctx* ctx, const double* u_dev, double* R_dev);
+
+/* y_dev = M x_dev, consistent mass of eq. material virtual work (first term), no Dirichlet treatment. */
+sdme_status sdme_mass_apply(sdme_ctx* ctx, const double* x_dev, double* y_dev);
+
+/*
+ * y_dev = (b1 M + K_T(u)) x_dev, the effective tangent of eq. NR_explicit
+ * (consistent linearisation, Sec. 3, eq. effective stiffness 2), with the
+ * rows and columns of constrained DOFs replaced by the identity.  Arithmetic
+ * in the context's precision (float32 contractions for SDME_MIXED_FP32).
+ */
+sdme_status sdme_tangent_apply(sdme_ctx* ctx, const double* u_dev, double b1, const double* x_dev,
+                               double* y_dev);
+
+/* d_dev = diag(b1 M + K_T(u)), 1 on constrained DOFs (Jacobi preconditioner of the CGD solver). */
+sdme_status sdme_diagonal(sdme_ctx* ctx, const double* u_dev, double b1, double* d_dev);
+
+/*
+ * Solve (b1 M + K_T(u)) x = b (constrained rows identity, b's constrained
+ * entries ignored and x's set to 0) by Jacobi-preconditioned CG from x = 0,
+ * stopping when ||r||_2 <= rtol ||b||_2 (CGD of Sec. 5).  Writes the
+ * iteration count and the final relative residual (host pointers, may be
+ * NULL).  SDME_PCG_MAXIT when maxit is reached.
+ */
+sdme_status sdme_pcg_solve(sdme_ctx* ctx, const double* u_dev, double b1, const double* b_dev,
+                           double* x_dev, double rtol, int maxit, int* iters, double* final_rel);
+
+/*
+ * Dead uniform traction t[3] on face `face` (SDME_XMIN..SDME_ZMAX):
+ * f_dev = int_face t . N_i dA (fourth term of eq. material virtual work).
+ * Overwrites f_dev (device, ndof).  Host-side quadrature, one upload.
+ */
+sdme_status sdme_traction_load(sdme_ctx* ctx, int face, const double t[3], double* f_dev);
+
+/*
+ * One implicit Newmark step t_n -> t_{n+1} solved by Newton-Raphson with
+ * Jacobi-PCG linear solves (Sec. 4.2, eqs. Eq:residual, NR_explicit):
+ *   psi = P_{n+1} - R(u^k) - M a(u^k),  a(u) = b1 (u - u_n) - b2 v_n - b3 a_n,
+ *   (b1 M + K_T(u^k)) du = psi,  u^{k+1} = u^k + du,
+ * predictor u^0 = u_n; then a_{n+1} and v_{n+1} by the Newmark formulas.
+ * P_next_dev: external load at t_{n+1} (device, ndof).  Constrained entries of
+ * state->u keep their values.  opts NULL selects defaults
+ * (0.25, 0.5, 1e-8, 30, 1e-10, 1e-4, 20000).  stats may be NULL.
+ */
+sdme_status sdme_implicit_newmark_step(sdme_ctx* ctx, sdme_state* state, double dt,
+                                       const double* P_next_dev, const sdme_newton_opts* opts,
+                                       sdme_step_stats* stats);
+
+/* Cumulative device event timings of the context (ms) and counts, for measurement. */
+typedef struct {
+  double tangent_ms;     /* sum of timed tangent-kernel launches */
+  int64_t tangent_launches;
+  int64_t kernel_launches; /* all kernels launched by this context */
+} sdme_timing;
+
+/* Enable (1) / disable (0) CUDA-event timing of every tangent-kernel launch. */
+sdme_status sdme_set_timing(sdme_ctx* ctx, int enable);
+sdme_status sdme_get_timing(sdme_ctx* ctx, sdme_timing* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDME_H */

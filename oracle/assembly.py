@@ -206,3 +206,26 @@ class Discretization:
         rhs = self.scatter(self.ref.project(func(self.gauss_points(), t)))
         M = self.mass_matrix() / self.rho
         return spla.spsolve(M.tocsc(), rhs)
+
+
+def elements_touching(mesh, dofs):
+    """Indices of the elements whose coefficient set contains any of ``dofs``
+    (used to evaluate sampled outputs of a large mesh element by element)."""
+    P = mesh.P
+    Nx, Ny, _ = mesh.N
+    out = set()
+    for g in np.atleast_1d(dofs):
+        r = int(g) % mesh.Nn
+        lat = (r % Nx, (r // Nx) % Ny, r // (Nx * Ny))
+        cand = []
+        for d in range(3):
+            i = lat[d]
+            es = {min(i // P, mesh.ne[d] - 1)}
+            if i % P == 0 and i > 0:
+                es.add(i // P - 1)
+            cand.append(sorted(es))
+        for ex in cand[0]:
+            for ey in cand[1]:
+                for ez in cand[2]:
+                    out.add((ez * mesh.ne[1] + ey) * mesh.ne[0] + ex)
+    return np.array(sorted(out), dtype=np.int64)

@@ -1,0 +1,241 @@
+"""Thin Python binding over the libsdme C ABI (include/sdme.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+sm_103a kernels.  Vectors are passed as torch CUDA float64 tensors (their
+device pointers); the library never sees torch types.  Importing this
+package loads libsdme.so and fails loudly when it is missing or was built
+without the entry points the header declares.
+
+Method: Dias, Suzuki, Valente, Bittencourt (arXiv:2104.13466): SDME 1D bases
+(Sec. 2), total-Lagrangian neo-Hookean elastodynamics (Sec. 3), Newmark +
+Newton with diagonal-preconditioned CG (Sec. 4.2, Sec. 5).
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsdme.so")
+
+# status codes (sdme_status)
+OK, EINVAL, ENOMEM, ECUDA, PCG_MAXIT, NEWTON_DIVERGED, NONPOSITIVE_J, NAN, TIMEOUT, EUNSUPPORTED = range(10)
+# basis kinds (sdme_basis_kind)
+NODAL, MODAL, SDME_M, SDME_K, SDME_H = range(5)
+KIND_NAMES = {"nodal": NODAL, "modal": MODAL, "sdme_m": SDME_M, "sdme_k": SDME_K, "sdme_h": SDME_H}
+# precisions (sdme_precision)
+FP64, MIXED_FP32 = 0, 1
+# faces
+XMIN, XMAX, YMIN, YMAX, ZMIN, ZMAX = range(6)
+FACE_NAMES = {"xmin": XMIN, "xmax": XMAX, "ymin": YMIN, "ymax": YMAX, "zmin": ZMIN, "zmax": ZMAX}
+
+EXPORTS = ("sdme_status_string", "sdme_build_basis1d", "sdme_create", "sdme_destroy", "sdme_get_sizes",
+           "sdme_internal_force", "sdme_mass_apply", "sdme_tangent_apply", "sdme_diagonal", "sdme_pcg_solve",
+           "sdme_traction_load", "sdme_implicit_newmark_step", "sdme_set_timing", "sdme_get_timing")
+
+
+class BasisDesc(ctypes.Structure):
+    _fields_ = [("P", ctypes.c_int), ("kind", ctypes.c_int), ("k", ctypes.c_double), ("lam", ctypes.c_double),
+                ("start_nodal", ctypes.c_int), ("jacobi_alpha", ctypes.c_double), ("jacobi_beta", ctypes.c_double)]
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("nelem", ctypes.c_int * 3), ("length", ctypes.c_double * 3), ("clamp", ctypes.c_uint * 6)]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("lam", ctypes.c_double), ("rho", ctypes.c_double)]
+
+
+class NewtonOpts(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("gamma", ctypes.c_double), ("newton_tol", ctypes.c_double),
+                ("max_newton", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("mixed_rtol", ctypes.c_double),
+                ("pcg_maxit", ctypes.c_int)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("pcg_iters_total", ctypes.c_int), ("matvecs", ctypes.c_int),
+                ("converged", ctypes.c_int), ("residual0", ctypes.c_double), ("residual_final", ctypes.c_double),
+                ("pcg_iters", ctypes.c_int * 32), ("residuals", ctypes.c_double * 33)]
+
+
+class State(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("a", ctypes.c_void_p)]
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("tangent_ms", ctypes.c_double), ("tangent_launches", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libsdme.so not built at %s; run `python -m paper_2104_13466_gb300.build` "
+                          "(there is no CPU fallback)" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    for name in EXPORTS:
+        if not hasattr(lib, name):
+            raise ImportError("libsdme.so lacks %s" % name)
+    vp, d, i, pd = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    lib.sdme_status_string.restype = ctypes.c_char_p
+    lib.sdme_status_string.argtypes = [i]
+    lib.sdme_build_basis1d.argtypes = [ctypes.POINTER(BasisDesc), i, pd, pd, pd, pd, pd, pd]
+    lib.sdme_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(MeshDesc), ctypes.POINTER(Material),
+                                ctypes.POINTER(BasisDesc), i, vp]
+    lib.sdme_destroy.argtypes = [vp]
+    lib.sdme_get_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int64)]
+    lib.sdme_internal_force.argtypes = [vp, vp, vp]
+    lib.sdme_mass_apply.argtypes = [vp, vp, vp]
+    lib.sdme_tangent_apply.argtypes = [vp, vp, d, vp, vp]
+    lib.sdme_diagonal.argtypes = [vp, vp, d, vp]
+    lib.sdme_pcg_solve.argtypes = [vp, vp, d, vp, vp, d, i, ctypes.POINTER(i), pd]
+    lib.sdme_traction_load.argtypes = [vp, i, pd, vp]
+    lib.sdme_implicit_newmark_step.argtypes = [vp, ctypes.POINTER(State), d, vp, ctypes.POINTER(NewtonOpts),
+                                               ctypes.POINTER(StepStats)]
+    lib.sdme_set_timing.argtypes = [vp, i]
+    lib.sdme_get_timing.argtypes = [vp, ctypes.POINTER(Timing)]
+    for name in EXPORTS:
+        if name != "sdme_status_string":
+            getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+class SdmeError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (where, lib.sdme_status_string(status).decode(), status))
+
+
+def _check(status, where, allow=()):
+    if status != OK and status not in allow:
+        raise SdmeError(status, where)
+    return status
+
+
+def _ptr(t):
+    """Device pointer of a contiguous float64 CUDA tensor."""
+    if not t.is_cuda or t.dtype.itemsize != 8 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def basis_desc(P, kind, k=0.5, lam=100.0, start_nodal=False, jacobi_alpha=1.0, jacobi_beta=1.0):
+    kind = KIND_NAMES[kind] if isinstance(kind, str) else int(kind)
+    return BasisDesc(int(P), kind, float(k), float(lam), int(bool(start_nodal)), float(jacobi_alpha),
+                     float(jacobi_beta))
+
+
+def build_basis1d(P, kind, Q=None, k=0.5, lam=100.0, start_nodal=False):
+    """Host-only 1D basis tables (lattice order); returns numpy arrays
+    (xq, wq, B, D, M1, K1)."""
+    import numpy as np
+    Q = Q or (P + 2)
+    n = P + 1
+    out = [np.zeros(Q), np.zeros(Q), np.zeros(Q * n), np.zeros(Q * n), np.zeros(n * n), np.zeros(n * n)]
+    ptrs = [o.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for o in out]
+    desc = basis_desc(P, kind, k, lam, start_nodal)
+    _check(lib.sdme_build_basis1d(ctypes.byref(desc), int(Q), *ptrs), "sdme_build_basis1d")
+    xq, wq, B, D, M1, K1 = out
+    return xq, wq, B.reshape(Q, n), D.reshape(Q, n), M1.reshape(n, n), K1.reshape(n, n)
+
+
+def mesh_desc(elems, lengths, clamp):
+    """clamp: dict face-name -> iterable of components."""
+    m = MeshDesc()
+    for d in range(3):
+        m.nelem[d] = int(elems[d])
+        m.length[d] = float(lengths[d])
+    for f, comps in (clamp or {}).items():
+        bits = 0
+        for c in comps:
+            bits |= 1 << int(c)
+        m.clamp[FACE_NAMES[f] if isinstance(f, str) else int(f)] = bits
+    return m
+
+
+class Context:
+    """Owns an sdme_ctx.  Methods mirror the C entry points."""
+
+    def __init__(self, elems, lengths, clamp, mu, lam, rho, P, kind, precision=FP64, k=0.5, lam_h=100.0,
+                 start_nodal=False, stream=None):
+        import torch
+        self._mesh = mesh_desc(elems, lengths, clamp)
+        self._mat = Material(float(mu), float(lam), float(rho))
+        self._basis = basis_desc(P, kind, k, lam_h, start_nodal)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.sdme_create(ctypes.byref(h), ctypes.byref(self._mesh), ctypes.byref(self._mat),
+                               ctypes.byref(self._basis), int(precision), ctypes.c_void_p(stream.cuda_stream)),
+               "sdme_create")
+        self._h = h
+        ndof = ctypes.c_int64()
+        N = (ctypes.c_int * 3)()
+        ne = ctypes.c_int64()
+        _check(lib.sdme_get_sizes(h, ctypes.byref(ndof), N, ctypes.byref(ne)), "sdme_get_sizes")
+        self.ndof, self.N, self.nelem = ndof.value, tuple(N), ne.value
+        self.P = P
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.sdme_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def internal_force(self, u, R):
+        return _check(lib.sdme_internal_force(self._h, _ptr(u), _ptr(R)), "sdme_internal_force")
+
+    def mass_apply(self, x, y):
+        return _check(lib.sdme_mass_apply(self._h, _ptr(x), _ptr(y)), "sdme_mass_apply")
+
+    def tangent_apply(self, u, b1, x, y):
+        return _check(lib.sdme_tangent_apply(self._h, _ptr(u), float(b1), _ptr(x), _ptr(y)), "sdme_tangent_apply")
+
+    def diagonal(self, u, b1, d):
+        return _check(lib.sdme_diagonal(self._h, _ptr(u), float(b1), _ptr(d)), "sdme_diagonal")
+
+    def pcg_solve(self, u, b1, b, x, rtol=1e-10, maxit=20000, allow_maxit=False):
+        its = ctypes.c_int()
+        rel = ctypes.c_double()
+        st = lib.sdme_pcg_solve(self._h, _ptr(u), float(b1), _ptr(b), _ptr(x), float(rtol), int(maxit),
+                                ctypes.byref(its), ctypes.byref(rel))
+        _check(st, "sdme_pcg_solve", allow=(PCG_MAXIT,) if allow_maxit else ())
+        return its.value, rel.value
+
+    def traction_load(self, face, t, f):
+        face = FACE_NAMES[face] if isinstance(face, str) else int(face)
+        tt = (ctypes.c_double * 3)(*[float(v) for v in t])
+        return _check(lib.sdme_traction_load(self._h, face, tt, _ptr(f)), "sdme_traction_load")
+
+    def implicit_newmark_step(self, u, v, a, dt, P_next, beta=0.25, gamma=0.5, newton_tol=1e-8, max_newton=30,
+                              pcg_rtol=1e-10, mixed_rtol=1e-4, pcg_maxit=20000, allow=()):
+        st = State(u.data_ptr(), v.data_ptr(), a.data_ptr())
+        for t in (u, v, a):
+            _ptr(t)
+        opts = NewtonOpts(beta, gamma, newton_tol, max_newton, pcg_rtol, mixed_rtol, pcg_maxit)
+        stats = StepStats()
+        status = lib.sdme_implicit_newmark_step(self._h, ctypes.byref(st), float(dt), _ptr(P_next),
+                                                ctypes.byref(opts), ctypes.byref(stats))
+        _check(status, "sdme_implicit_newmark_step", allow=allow)
+        n = min(stats.newton_iters, 32)
+        return {"status": status, "newton_iters": stats.newton_iters, "pcg_iters_total": stats.pcg_iters_total,
+                "matvecs": stats.matvecs, "converged": bool(stats.converged), "residual0": stats.residual0,
+                "residual_final": stats.residual_final, "pcg_iters": list(stats.pcg_iters[:n]),
+                "residuals": list(stats.residuals[:n + 1])}
+
+    def set_timing(self, enable=True):
+        return _check(lib.sdme_set_timing(self._h, int(bool(enable))), "sdme_set_timing")
+
+    def timing(self):
+        t = Timing()
+        _check(lib.sdme_get_timing(self._h, ctypes.byref(t)), "sdme_get_timing")
+        return {"tangent_ms": t.tangent_ms, "tangent_launches": t.tangent_launches,
+                "kernel_launches": t.kernel_launches}

@@ -1,0 +1,574 @@
+// C ABI of the engine: context set-up, the public operators, Jacobi-PCG and
+// the Newton-Newmark driver.  All device work goes through the element
+// kernels (elem_p<P>.cu) and the per-DOF kernels (vec_kernels.cuh).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/sdme.h"
+#include "basis1d.h"
+#include "common.cuh"
+#include "elem_launch.h"
+#include "vec_kernels.cuh"
+
+using namespace sdme;
+
+namespace {
+
+constexpr int kVecBlocks = 152 * 4;      // per-DOF grid: 4 CTAs of 256 threads per SM
+constexpr int kPcgChunk = 8;             // iterations issued between host status reads
+
+#define SDME_CUDA(call)                                           \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) {                                      \
+      ctx->last_cuda = e_;                                        \
+      return SDME_ECUDA;                                          \
+    }                                                             \
+  } while (0)
+
+#define SDME_TRY(call)              \
+  do {                              \
+    sdme_status s_ = (call);        \
+    if (s_ != SDME_OK) return s_;   \
+  } while (0)
+
+}  // namespace
+
+struct sdme_ctx {
+  sdme_mesh_desc mesh{};
+  sdme_material mat{};
+  sdme_basis_desc basis{};
+  sdme_precision prec = SDME_FP64;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaError_t last_cuda = cudaSuccess;
+
+  HostElemData h;
+  MeshInfo mi{};
+  int64_t ndof = 0;
+  int Q = 0;
+
+  // device buffers
+  double* st64 = nullptr;
+  float* st32 = nullptr;
+  int* err = nullptr;
+  PcgScalars* scal = nullptr;
+  double* partial = nullptr;    // per-element / per-CTA partial sums
+  double* dscal = nullptr;      // [0]: norm^2 results ; counters follow
+  unsigned int* dcount = nullptr;
+  // PCG vectors
+  double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr, *d64 = nullptr, *x64 = nullptr;
+  float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr, *x32 = nullptr;
+  // Newton work vectors
+  double *un = nullptr, *ahat = nullptr, *mhat = nullptr, *y = nullptr, *psi = nullptr, *du = nullptr;
+  // pinned host mirrors
+  PcgScalars* scal_h = nullptr;
+  double* dscal_h = nullptr;
+  int* err_h = nullptr;
+
+  // measurement
+  bool timing = false;
+  double tangent_ms = 0.0;
+  int64_t tangent_launches = 0;
+  int64_t kernel_launches = 0;
+  std::vector<cudaEvent_t> ev;
+};
+
+namespace {
+
+template <typename F>
+cudaError_t dispatch_P(int P, F&& f) {
+  switch (P) {
+    case 1: return f(std::integral_constant<int, 1>());
+    case 2: return f(std::integral_constant<int, 2>());
+    case 3: return f(std::integral_constant<int, 3>());
+    case 4: return f(std::integral_constant<int, 4>());
+    case 5: return f(std::integral_constant<int, 5>());
+    case 6: return f(std::integral_constant<int, 6>());
+    case 7: return f(std::integral_constant<int, 7>());
+    case 8: return f(std::integral_constant<int, 8>());
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+sdme_status check_basis(const sdme_basis_desc* b) {
+  if (!b || b->P < 1 || b->P > kMaxP || b->kind < SDME_NODAL || b->kind > SDME_SDME_H) return SDME_EINVAL;
+  if (b->kind >= SDME_SDME_M && (b->k < 0.0 || b->k > 1.0)) return SDME_EINVAL;
+  return SDME_OK;
+}
+
+bool build_basis(const sdme_basis_desc* b, Basis1D& out) {
+  return out.build(b->P, (int)b->kind, b->k, b->lambda, b->start_nodal != 0, b->jacobi_alpha, b->jacobi_beta);
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+}
+
+sdme_status residual_launch(sdme_ctx* ctx, double b1, const double* u, double* y) {
+  const HostElemData& h = ctx->h;
+  float* st32 = (ctx->prec == SDME_MIXED_FP32) ? ctx->st32 : nullptr;
+  SDME_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * ctx->ndof, ctx->stream));
+  SDME_CUDA(dispatch_P(h.P, [&](auto Pc) {
+    return launch_residual<decltype(Pc)::value>(h, b1, u, y, ctx->st64, st32, ctx->err, ctx->stream);
+  }));
+  ctx->kernel_launches += 1;
+  return SDME_OK;
+}
+
+sdme_status sync_and_check(sdme_ctx* ctx) {
+  SDME_CUDA(cudaMemcpyAsync(ctx->err_h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  SDME_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (*ctx->err_h) {
+    SDME_CUDA(cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream));
+    return SDME_NONPOSITIVE_J;
+  }
+  return SDME_OK;
+}
+
+template <typename T, typename TV>
+sdme_status tangent_launch(sdme_ctx* ctx, double b1, const TV* x, TV* y, double* partial, PcgScalars* scal,
+                           cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
+  const HostElemData& h = ctx->h;
+  const T* st;
+  if constexpr (sizeof(T) == 8) st = ctx->st64;
+  else st = ctx->st32;
+  if (e0) SDME_CUDA(cudaEventRecord(e0, ctx->stream));
+  SDME_CUDA(dispatch_P(h.P, [&](auto Pc) {
+    return launch_tangent<decltype(Pc)::value, T, TV>(h, b1, x, y, st, partial, scal, ctx->stream);
+  }));
+  if (e1) SDME_CUDA(cudaEventRecord(e1, ctx->stream));
+  ctx->kernel_launches += 1;
+  return SDME_OK;
+}
+
+template <typename T>
+sdme_status diag_launch(sdme_ctx* ctx, double b1, T* d, int inverse) {
+  const HostElemData& h = ctx->h;
+  const T* st;
+  if constexpr (sizeof(T) == 8) st = ctx->st64;
+  else st = ctx->st32;
+  SDME_CUDA(cudaMemsetAsync(d, 0, sizeof(T) * ctx->ndof, ctx->stream));
+  SDME_CUDA(dispatch_P(h.P, [&](auto Pc) {
+    return launch_diag<decltype(Pc)::value, T>(h, b1, st, d, ctx->stream);
+  }));
+  k_diag_finish<T><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, d, inverse);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 2;
+  return SDME_OK;
+}
+
+// ||x||^2 on the host (synchronises)
+sdme_status norm2_host(sdme_ctx* ctx, const double* x, double* out) {
+  k_norm2<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, x, ctx->partial, ctx->dcount, ctx->dscal);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 1;
+  SDME_CUDA(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  SDME_CUDA(cudaStreamSynchronize(ctx->stream));
+  *out = ctx->dscal_h[0];
+  return SDME_OK;
+}
+
+// Jacobi PCG on (b1 M + K_T) with the linearisation state already stored.
+// b and x are float64 device vectors; the iteration runs in TV / T.
+template <typename T, typename TV>
+sdme_status pcg_core(sdme_ctx* ctx, double b1, const double* b, double* x, double rtol, int maxit, int* iters,
+                     double* rel, TV* r, TV* p, TV* q, TV* dinv, TV* xv) {
+  SDME_TRY(diag_launch<T>(ctx, b1, (T*)dinv, 1));
+  k_pcg_init<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, b, 1.0, dinv, xv, r, p, q, ctx->scal,
+                                                              ctx->partial, rtol, maxit);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 1;
+  int done_iters = 0;
+  for (;;) {
+    const bool tim = ctx->timing;
+    for (int j = 0; j < kPcgChunk; ++j) {
+      SDME_TRY((tangent_launch<T, TV>(ctx, b1, p, q, ctx->partial, ctx->scal, tim ? ctx->ev[2 * j] : nullptr,
+                                      tim ? ctx->ev[2 * j + 1] : nullptr)));
+      k_pcg_update<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, xv, r, p, q, dinv, ctx->scal,
+                                                                    ctx->partial);
+      k_pcg_direction<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, r, dinv, p, ctx->scal);
+      ctx->kernel_launches += 2;
+    }
+    SDME_CUDA(cudaGetLastError());
+    SDME_CUDA(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(PcgScalars), cudaMemcpyDeviceToHost, ctx->stream));
+    SDME_CUDA(cudaStreamSynchronize(ctx->stream));
+    const PcgScalars& s = *ctx->scal_h;
+    if (tim) {
+      // tangent launches of this chunk that ran with a live iteration: one per
+      // completed iteration, plus the one that detected a breakdown
+      int ran = s.iter - done_iters + (s.status == kPcgBreakdown ? 1 : 0);
+      if (ran > kPcgChunk) ran = kPcgChunk;
+      for (int j = 0; j < ran; ++j) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev[2 * j], ctx->ev[2 * j + 1]) == cudaSuccess) {
+          ctx->tangent_ms += ms;
+          ctx->tangent_launches += 1;
+        }
+      }
+    }
+    done_iters = s.iter;
+    if (s.status != kPcgRunning) break;
+  }
+  const PcgScalars& s = *ctx->scal_h;
+  if (iters) *iters = s.iter;
+  if (rel) *rel = (s.bb > 0.0) ? std::sqrt(s.rr / s.bb) : 0.0;
+  k_to_double<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, xv, 1.0, x);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 1;
+  if (s.status == kPcgBreakdown) return SDME_NAN;
+  if (s.status == kPcgMaxit) return SDME_PCG_MAXIT;
+  return SDME_OK;
+}
+
+sdme_status pcg_dispatch(sdme_ctx* ctx, double b1, const double* b, double* x, double rtol, int maxit,
+                         int* iters, double* rel) {
+  if (ctx->prec == SDME_MIXED_FP32)
+    return pcg_core<float, float>(ctx, b1, b, x, rtol, maxit, iters, rel, ctx->r32, ctx->p32, ctx->q32, ctx->d32,
+                                  ctx->x32);
+  return pcg_core<double, double>(ctx, b1, b, x, rtol, maxit, iters, rel, ctx->r64, ctx->p64, ctx->q64, ctx->d64,
+                                  ctx->x64);
+}
+
+void free_all(sdme_ctx* ctx) {
+  void* dev[] = {ctx->st64, ctx->st32, ctx->err, ctx->scal, ctx->partial, ctx->dscal, ctx->dcount,
+                 ctx->r64, ctx->p64, ctx->q64, ctx->d64, ctx->x64, ctx->r32, ctx->p32, ctx->q32, ctx->d32,
+                 ctx->x32, ctx->un, ctx->ahat, ctx->mhat, ctx->y, ctx->psi, ctx->du};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  if (ctx->scal_h) cudaFreeHost(ctx->scal_h);
+  if (ctx->dscal_h) cudaFreeHost(ctx->dscal_h);
+  if (ctx->err_h) cudaFreeHost(ctx->err_h);
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sdme_status_string(sdme_status s) {
+  switch (s) {
+    case SDME_OK: return "ok";
+    case SDME_EINVAL: return "invalid argument";
+    case SDME_ENOMEM: return "out of memory";
+    case SDME_ECUDA: return "CUDA runtime error";
+    case SDME_PCG_MAXIT: return "PCG reached maxit";
+    case SDME_NEWTON_DIVERGED: return "Newton did not converge";
+    case SDME_NONPOSITIVE_J: return "non-positive Jacobian det F";
+    case SDME_NAN: return "non-finite value";
+    case SDME_TIMEOUT: return "device wait timed out";
+    case SDME_EUNSUPPORTED: return "unsupported option";
+  }
+  return "unknown status";
+}
+
+sdme_status sdme_build_basis1d(const sdme_basis_desc* basis, int Q, double* xq, double* wq, double* B, double* D,
+                               double* M1, double* K1) {
+  if (check_basis(basis) != SDME_OK || Q < 1 || Q > 16) return SDME_EINVAL;
+  Basis1D b;
+  if (!build_basis(basis, b)) return SDME_EINVAL;
+  std::vector<double> x(Q), w(Q);
+  gauss_legendre(Q, x.data(), w.data());
+  if (xq) std::memcpy(xq, x.data(), sizeof(double) * Q);
+  if (wq) std::memcpy(wq, w.data(), sizeof(double) * Q);
+  b.tables(Q, x.data(), B, D);
+  if (M1 || K1) {
+    std::vector<double> M, K;
+    b.matrices(M, K, true);
+    const int n = b.n;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const int pi = b.lattice_to_paper(i), pj = b.lattice_to_paper(j);
+        if (M1) M1[i * n + j] = M[pi * n + pj];
+        if (K1) K1[i * n + j] = K[pi * n + pj];
+      }
+  }
+  return SDME_OK;
+}
+
+sdme_status sdme_create(sdme_ctx** out, const sdme_mesh_desc* mesh, const sdme_material* mat,
+                        const sdme_basis_desc* basis, sdme_precision prec, void* stream) {
+  if (!out || !mesh || !mat) return SDME_EINVAL;
+  *out = nullptr;
+  if (check_basis(basis) != SDME_OK) return SDME_EINVAL;
+  if (prec != SDME_FP64 && prec != SDME_MIXED_FP32) return SDME_EINVAL;
+  for (int d = 0; d < 3; ++d)
+    if (mesh->nelem[d] < 1 || !(mesh->length[d] > 0.0)) return SDME_EINVAL;
+  if (!(mat->mu > 0.0) || !(mat->lambda >= 0.0) || !(mat->rho >= 0.0)) return SDME_EINVAL;
+  const int P = basis->P, n = P + 1, Q = P + 2;
+  int64_t N[3];
+  for (int d = 0; d < 3; ++d) N[d] = (int64_t)mesh->nelem[d] * P + 1;
+  const int64_t nelem = (int64_t)mesh->nelem[0] * mesh->nelem[1] * mesh->nelem[2];
+  if (nelem > 0x7fffffff || N[0] * N[1] * N[2] * 3 > ((int64_t)1 << 40)) return SDME_EINVAL;
+
+  sdme_ctx* ctx = new (std::nothrow) sdme_ctx();
+  if (!ctx) return SDME_ENOMEM;
+  ctx->mesh = *mesh;
+  ctx->mat = *mat;
+  ctx->basis = *basis;
+  ctx->prec = prec;
+  Basis1D b;
+  if (!build_basis(basis, b)) {
+    delete ctx;
+    return SDME_EINVAL;
+  }
+  HostElemData& h = ctx->h;
+  h.P = P;
+  h.nelem = (int)nelem;
+  h.B.resize(Q * n);
+  h.D.resize(Q * n);
+  h.DQ.resize(Q * Q);
+  h.W.resize(Q);
+  std::vector<double> xq(Q);
+  gauss_legendre(Q, xq.data(), h.W.data());
+  b.tables(Q, xq.data(), h.B.data(), h.D.data());
+  collocation_derivative(Q, xq.data(), h.DQ.data());
+  double hh[3];
+  for (int d = 0; d < 3; ++d) {
+    hh[d] = mesh->length[d] / mesh->nelem[d];
+    h.s[d] = 2.0 / hh[d];
+    h.ne[d] = mesh->nelem[d];
+    h.N[d] = (int)N[d];
+    ctx->mi.N[d] = (int)N[d];
+  }
+  h.detJ = hh[0] * hh[1] * hh[2] / 8.0;
+  h.mu = mat->mu;
+  h.lam = mat->lambda;
+  h.rho = mat->rho;
+  h.Nn = N[0] * N[1] * N[2];
+  for (int f = 0; f < 6; ++f) h.clamp[f] = ctx->mi.clamp[f] = mesh->clamp[f] & 7u;
+  ctx->mi.Nn = h.Nn;
+  ctx->mi.ndof = 3 * h.Nn;
+  ctx->ndof = 3 * h.Nn;
+  ctx->Q = Q;
+
+  // NULL is the legacy default stream, which orders with every other
+  // blocking stream of the process (torch's default stream included).
+  ctx->stream = (cudaStream_t)stream;
+  ctx->own_stream = false;
+  const int64_t nst = nelem * kStateFields * (int64_t)Q * Q * Q;
+  const int64_t nd = ctx->ndof;
+  const int64_t npart = std::max<int64_t>(nelem, 2 * kVecBlocks) + 64;
+  bool ok = true;
+  ok = ok && dalloc(&ctx->st64, nst) == cudaSuccess;
+  if (prec == SDME_MIXED_FP32) ok = ok && dalloc(&ctx->st32, nst) == cudaSuccess;
+  ok = ok && dalloc(&ctx->err, 1) == cudaSuccess;
+  ok = ok && dalloc(&ctx->scal, 1) == cudaSuccess;
+  ok = ok && dalloc(&ctx->partial, npart) == cudaSuccess;
+  ok = ok && dalloc(&ctx->dscal, 8) == cudaSuccess;
+  ok = ok && dalloc(&ctx->dcount, 8) == cudaSuccess;
+  if (prec == SDME_MIXED_FP32) {
+    ok = ok && dalloc(&ctx->r32, nd) == cudaSuccess && dalloc(&ctx->p32, nd) == cudaSuccess &&
+         dalloc(&ctx->q32, nd) == cudaSuccess && dalloc(&ctx->d32, nd) == cudaSuccess &&
+         dalloc(&ctx->x32, nd) == cudaSuccess;
+  } else {
+    ok = ok && dalloc(&ctx->r64, nd) == cudaSuccess && dalloc(&ctx->p64, nd) == cudaSuccess &&
+         dalloc(&ctx->q64, nd) == cudaSuccess && dalloc(&ctx->d64, nd) == cudaSuccess &&
+         dalloc(&ctx->x64, nd) == cudaSuccess;
+  }
+  ok = ok && dalloc(&ctx->un, nd) == cudaSuccess && dalloc(&ctx->ahat, nd) == cudaSuccess &&
+       dalloc(&ctx->mhat, nd) == cudaSuccess && dalloc(&ctx->y, nd) == cudaSuccess &&
+       dalloc(&ctx->psi, nd) == cudaSuccess && dalloc(&ctx->du, nd) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&ctx->scal_h, sizeof(PcgScalars)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&ctx->dscal_h, 8 * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&ctx->err_h, sizeof(int)) == cudaSuccess;
+  if (ok) {
+    ctx->ev.resize(2 * kPcgChunk);
+    for (auto& e : ctx->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+  }
+  if (ok) {
+    ok = cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream) == cudaSuccess &&
+         cudaMemsetAsync(ctx->scal, 0, sizeof(PcgScalars), ctx->stream) == cudaSuccess &&
+         cudaMemsetAsync(ctx->dcount, 0, 8 * sizeof(unsigned int), ctx->stream) == cudaSuccess &&
+         cudaStreamSynchronize(ctx->stream) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    free_all(ctx);
+    delete ctx;
+    return SDME_ENOMEM;
+  }
+  *out = ctx;
+  return SDME_OK;
+}
+
+sdme_status sdme_destroy(sdme_ctx* ctx) {
+  if (!ctx) return SDME_EINVAL;
+  cudaStreamSynchronize(ctx->stream);
+  free_all(ctx);
+  delete ctx;
+  return SDME_OK;
+}
+
+sdme_status sdme_get_sizes(const sdme_ctx* ctx, int64_t* ndof, int N[3], int64_t* nelem) {
+  if (!ctx) return SDME_EINVAL;
+  if (ndof) *ndof = ctx->ndof;
+  if (N)
+    for (int d = 0; d < 3; ++d) N[d] = ctx->h.N[d];
+  if (nelem) *nelem = ctx->h.nelem;
+  return SDME_OK;
+}
+
+sdme_status sdme_internal_force(sdme_ctx* ctx, const double* u_dev, double* R_dev) {
+  if (!ctx || !u_dev || !R_dev) return SDME_EINVAL;
+  SDME_TRY(residual_launch(ctx, 0.0, u_dev, R_dev));
+  return sync_and_check(ctx);
+}
+
+sdme_status sdme_mass_apply(sdme_ctx* ctx, const double* x_dev, double* y_dev) {
+  if (!ctx || !x_dev || !y_dev) return SDME_EINVAL;
+  SDME_CUDA(cudaMemsetAsync(y_dev, 0, sizeof(double) * ctx->ndof, ctx->stream));
+  SDME_CUDA(dispatch_P(ctx->h.P, [&](auto Pc) {
+    return launch_mass<decltype(Pc)::value>(ctx->h, x_dev, y_dev, ctx->stream);
+  }));
+  ctx->kernel_launches += 1;
+  return SDME_OK;
+}
+
+sdme_status sdme_tangent_apply(sdme_ctx* ctx, const double* u_dev, double b1, const double* x_dev, double* y_dev) {
+  if (!ctx || !u_dev || !x_dev || !y_dev) return SDME_EINVAL;
+  SDME_TRY(residual_launch(ctx, 0.0, u_dev, ctx->y));
+  SDME_TRY(sync_and_check(ctx));
+  k_mask_init<double><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, x_dev, y_dev);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 1;
+  if (ctx->prec == SDME_MIXED_FP32) return tangent_launch<float, double>(ctx, b1, x_dev, y_dev, nullptr, nullptr);
+  return tangent_launch<double, double>(ctx, b1, x_dev, y_dev, nullptr, nullptr);
+}
+
+sdme_status sdme_diagonal(sdme_ctx* ctx, const double* u_dev, double b1, double* d_dev) {
+  if (!ctx || !u_dev || !d_dev) return SDME_EINVAL;
+  SDME_TRY(residual_launch(ctx, 0.0, u_dev, ctx->y));
+  SDME_TRY(sync_and_check(ctx));
+  return diag_launch<double>(ctx, b1, d_dev, 0);
+}
+
+sdme_status sdme_pcg_solve(sdme_ctx* ctx, const double* u_dev, double b1, const double* b_dev, double* x_dev,
+                           double rtol, int maxit, int* iters, double* final_rel) {
+  if (!ctx || !u_dev || !b_dev || !x_dev || maxit < 1 || !(rtol >= 0.0)) return SDME_EINVAL;
+  SDME_TRY(residual_launch(ctx, 0.0, u_dev, ctx->y));
+  SDME_TRY(sync_and_check(ctx));
+  return pcg_dispatch(ctx, b1, b_dev, x_dev, rtol, maxit, iters, final_rel);
+}
+
+sdme_status sdme_traction_load(sdme_ctx* ctx, int face, const double t[3], double* f_dev) {
+  if (!ctx || !t || !f_dev || face < 0 || face > 5) return SDME_EINVAL;
+  const HostElemData& h = ctx->h;
+  const int P = h.P, n = P + 1, Q = ctx->Q;
+  // 1D integrals I_j = int_{-1}^{1} phi_j
+  std::vector<double> I(n, 0.0);
+  for (int q = 0; q < Q; ++q)
+    for (int j = 0; j < n; ++j) I[j] += h.W[q] * h.B[q * n + j];
+  const int axis = face / 2, side = face % 2;
+  const int ta = (axis == 0) ? 1 : 0, tb = (axis == 2) ? 1 : 2;
+  const double hl[3] = {ctx->mesh.length[0] / ctx->mesh.nelem[0], ctx->mesh.length[1] / ctx->mesh.nelem[1],
+                        ctx->mesh.length[2] / ctx->mesh.nelem[2]};
+  const double jac = 0.25 * hl[ta] * hl[tb];
+  std::vector<double> f(ctx->ndof, 0.0);
+  const int fixed = side ? h.N[axis] - 1 : 0;
+  for (int ea = 0; ea < h.ne[ta]; ++ea)
+    for (int eb = 0; eb < h.ne[tb]; ++eb)
+      for (int a = 0; a < n; ++a)
+        for (int bq = 0; bq < n; ++bq) {
+          int idx[3];
+          idx[axis] = fixed;
+          idx[ta] = ea * P + a;
+          idx[tb] = eb * P + bq;
+          const int64_t node = ((int64_t)idx[2] * h.N[1] + idx[1]) * h.N[0] + idx[0];
+          const double w = jac * I[a] * I[bq];
+          for (int c = 0; c < 3; ++c) f[c * h.Nn + node] += t[c] * w;
+        }
+  SDME_CUDA(cudaMemcpyAsync(f_dev, f.data(), sizeof(double) * ctx->ndof, cudaMemcpyHostToDevice, ctx->stream));
+  SDME_CUDA(cudaStreamSynchronize(ctx->stream));
+  return SDME_OK;
+}
+
+sdme_status sdme_implicit_newmark_step(sdme_ctx* ctx, sdme_state* state, double dt, const double* P_next_dev,
+                                       const sdme_newton_opts* opts, sdme_step_stats* stats) {
+  if (!ctx || !state || !state->u || !state->v || !state->a || !P_next_dev || !(dt > 0.0)) return SDME_EINVAL;
+  sdme_newton_opts o{0.25, 0.5, 1e-8, 30, 1e-10, 1e-4, 20000};
+  if (opts) o = *opts;
+  if (!(o.beta > 0.0) || o.max_newton < 0 || o.pcg_maxit < 1) return SDME_EINVAL;
+  sdme_step_stats st{};
+  const int64_t nd = ctx->ndof;
+  const double b1 = 1.0 / (o.beta * dt * dt), b2 = 1.0 / (o.beta * dt), b3 = (1.0 - 2.0 * o.beta) / (2.0 * o.beta);
+  cudaStream_t s = ctx->stream;
+  SDME_CUDA(cudaMemcpyAsync(ctx->un, state->u, sizeof(double) * nd, cudaMemcpyDeviceToDevice, s));
+  k_newmark_ahat<<<kVecBlocks, kVecThreads, 0, s>>>(nd, ctx->un, state->v, state->a, b1, b2, b3, ctx->ahat);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 1;
+  SDME_TRY(sdme_mass_apply(ctx, ctx->ahat, ctx->mhat));
+  double pn2 = 0.0;
+  SDME_TRY(norm2_host(ctx, P_next_dev, &pn2));
+  const double pnorm = std::sqrt(pn2);
+  const double inner_rtol = (ctx->prec == SDME_MIXED_FP32) ? o.mixed_rtol : o.pcg_rtol;
+  double psi0 = -1.0;
+  sdme_status result = SDME_NEWTON_DIVERGED;
+  for (int k = 0; k <= o.max_newton; ++k) {
+    SDME_TRY(residual_launch(ctx, b1, state->u, ctx->y));
+    k_residual_combine<<<kVecBlocks, kVecThreads, 0, s>>>(ctx->mi, P_next_dev, ctx->mhat, ctx->y, ctx->psi,
+                                                        ctx->partial, ctx->dcount, ctx->dscal);
+    SDME_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 1;
+    SDME_CUDA(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SDME_TRY(sync_and_check(ctx));
+    const double nrm = std::sqrt(ctx->dscal_h[0]);
+    if (!std::isfinite(nrm)) {
+      result = SDME_NAN;
+      break;
+    }
+    if (psi0 < 0.0) psi0 = nrm;
+    if (k < 33) st.residuals[k] = nrm;
+    st.residual_final = nrm;
+    st.newton_iters = k;
+    if (nrm <= o.newton_tol * std::max(psi0, 1e-14 * pnorm)) {
+      result = SDME_OK;
+      st.converged = 1;
+      break;
+    }
+    if (k == o.max_newton) break;
+    int its = 0;
+    double rel = 0.0;
+    sdme_status ps = pcg_dispatch(ctx, b1, ctx->psi, ctx->du, inner_rtol, o.pcg_maxit, &its, &rel);
+    if (ps != SDME_OK && ps != SDME_PCG_MAXIT) {
+      result = ps;
+      break;
+    }
+    if (k < 32) st.pcg_iters[k] = its;
+    st.pcg_iters_total += its;
+    st.matvecs += its;
+    k_axpy<double><<<kVecBlocks, kVecThreads, 0, s>>>(nd, 1.0, ctx->du, state->u);
+    SDME_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 1;
+  }
+  st.residual0 = psi0;
+  k_newmark_final<<<kVecBlocks, kVecThreads, 0, s>>>(nd, state->u, ctx->ahat, b1, dt, o.gamma, state->v, state->a);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 1;
+  SDME_CUDA(cudaStreamSynchronize(s));
+  if (stats) *stats = st;
+  return result;
+}
+
+sdme_status sdme_set_timing(sdme_ctx* ctx, int enable) {
+  if (!ctx) return SDME_EINVAL;
+  ctx->timing = enable != 0;
+  return SDME_OK;
+}
+
+sdme_status sdme_get_timing(sdme_ctx* ctx, sdme_timing* out) {
+  if (!ctx || !out) return SDME_EINVAL;
+  out->tangent_ms = ctx->tangent_ms;
+  out->tangent_launches = ctx->tangent_launches;
+  out->kernel_launches = ctx->kernel_launches;
+  return SDME_OK;
+}
+
+}  // extern "C"

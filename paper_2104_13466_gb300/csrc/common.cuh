@@ -1,0 +1,132 @@
+// Device helpers shared by the element and vector kernels: reductions,
+// the last-CTA-done pattern and the PCG scalar block.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sdme {
+
+// Linearisation state layout per element: [10][Q^3]: H = F^{-T} (9, row
+// major iJ) then c = mu - lambda ln J.
+constexpr int kStateFields = 10;
+
+// PCG status values held in PcgScalars::status
+constexpr int kPcgRunning = 0;
+constexpr int kPcgConverged = 1;
+constexpr int kPcgMaxit = 2;
+constexpr int kPcgBreakdown = 3;   // non-positive or non-finite curvature / residual
+
+// Scalars of one Jacobi-PCG solve, resident in device memory so that an
+// iteration needs no host round trip.  All float64.
+struct PcgScalars {
+  double rz;       // r . z of the current iterate
+  double pq;       // p . (A p)
+  double rr;       // r . r
+  double bb;       // b . b (of the scaled right-hand side)
+  double alpha, beta;
+  double tol2;     // rtol^2 * bb
+  int iter, maxit;
+  int status;
+  unsigned int counter;   // last-CTA counters (reset by the finishing CTA)
+  unsigned int counter2;
+  int pad;
+};
+
+// Lattice description used by per-DOF kernels.
+struct MeshInfo {
+  int N[3];
+  int64_t Nn;
+  int64_t ndof;
+  unsigned clamp[6];
+};
+
+__device__ __forceinline__ bool dof_constrained(const MeshInfo& m, int64_t g) {
+  const int c = (int)(g / m.Nn);
+  const int64_t r = g - (int64_t)c * m.Nn;
+  const int ix = (int)(r % m.N[0]);
+  const int64_t t = r / m.N[0];
+  const int iy = (int)(t % m.N[1]);
+  const int iz = (int)(t / m.N[1]);
+  const unsigned bit = 1u << c;
+  return ((ix == 0) && (m.clamp[0] & bit)) || ((ix == m.N[0] - 1) && (m.clamp[1] & bit)) ||
+         ((iy == 0) && (m.clamp[2] & bit)) || ((iy == m.N[1] - 1) && (m.clamp[3] & bit)) ||
+         ((iz == 0) && (m.clamp[4] & bit)) || ((iz == m.N[2] - 1) && (m.clamp[5] & bit));
+}
+
+// Sum over the CTA (float64); result valid in every thread.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red_[32];
+  __shared__ double out_;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red_[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = (threadIdx.x < ((blockDim.x + 31) >> 5)) ? red_[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) out_ = w;
+  }
+  __syncthreads();
+  return out_;
+}
+
+// Two sums at once.
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double ra_[32], rb_[32];
+  __shared__ double oa_, ob_;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    ra_[threadIdx.x >> 5] = a;
+    rb_[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const bool ok = threadIdx.x < ((blockDim.x + 31) >> 5);
+    double x = ok ? ra_[threadIdx.x] : 0.0, y = ok ? rb_[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    if (threadIdx.x == 0) {
+      oa_ = x;
+      ob_ = y;
+    }
+  }
+  __syncthreads();
+  a = oa_;
+  b = ob_;
+}
+
+// Call after thread 0 of every CTA has written its partial(s).  Returns
+// true in every thread of the last CTA to arrive; that CTA must reset the
+// counter.  Nothing waits: CTAs that are not last simply return false.
+__device__ __forceinline__ bool last_block_done(unsigned int* counter) {
+  __shared__ bool last_;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int t = atomicAdd(counter, 1u);
+    last_ = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last_) __threadfence();
+  return last_;
+}
+
+// Deterministic sum of m partials (fixed strided order + fixed tree).
+__device__ __forceinline__ double ordered_sum(const double* part, int m) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) s += ((const volatile double*)part)[i];
+  return block_sum(s);
+}
+
+}  // namespace sdme

@@ -1,0 +1,118 @@
+// Host-side launch wrappers for the element kernels, instantiated once per
+// polynomial order in elem_p<P>.cu.
+#pragma once
+
+#include "elem_kernels.cuh"
+#include "elem_launch.h"
+
+namespace sdme {
+
+template <typename T, int P>
+static ElemParams<T, P> make_params(const HostElemData& h, double b1) {
+  ElemParams<T, P> p;
+  constexpr int n = P + 1, Q = P + 2;
+  for (int i = 0; i < Q * n; ++i) {
+    p.tab.B[i] = (T)h.B[i];
+    p.tab.D[i] = (T)h.D[i];
+  }
+  for (int i = 0; i < Q * Q; ++i) p.tab.DQ[i] = (T)h.DQ[i];
+  for (int i = 0; i < Q; ++i) p.tab.W[i] = (T)h.W[i];
+  for (int d = 0; d < 3; ++d) {
+    p.s[d] = (T)h.s[d];
+    p.ne[d] = h.ne[d];
+    p.N[d] = h.N[d];
+  }
+  p.detJ = (T)h.detJ;
+  p.mu = (T)h.mu;
+  p.lam = (T)h.lam;
+  p.rho = (T)h.rho;
+  p.b1 = (T)b1;
+  p.Nn = h.Nn;
+  for (int f = 0; f < 6; ++f) p.clamp[f] = h.clamp[f];
+  return p;
+}
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+template <int P>
+cudaError_t launch_residual(const HostElemData& h, double b1, const double* u, double* y, double* st64,
+                            float* st32, int* err, cudaStream_t s) {
+  static bool init = false;
+  const size_t smem = sizeof(double) * elem_smem_words<P>();
+  if (!init) {
+    cudaError_t e = set_smem(residual_kernel<P>, smem);
+    if (e != cudaSuccess) return e;
+    init = true;
+  }
+  auto prm = make_params<double, P>(h, b1);
+  residual_kernel<P><<<h.nelem, elem_threads(P), smem, s>>>(prm, u, y, st64, st32, err);
+  return cudaGetLastError();
+}
+
+template <int P, typename T, typename TV>
+cudaError_t launch_tangent(const HostElemData& h, double b1, const TV* x, TV* y, const T* st,
+                           double* partial, PcgScalars* scal, cudaStream_t s) {
+  static bool init = false;
+  const size_t smem = sizeof(T) * elem_smem_words<P>();
+  if (!init) {
+    cudaError_t e = set_smem(tangent_kernel<P, T, TV>, smem);
+    if (e != cudaSuccess) return e;
+    init = true;
+  }
+  auto prm = make_params<T, P>(h, b1);
+  tangent_kernel<P, T, TV><<<h.nelem, elem_threads(P), smem, s>>>(prm, x, y, st, partial, scal);
+  return cudaGetLastError();
+}
+
+template <int P, typename T>
+cudaError_t launch_diag(const HostElemData& h, double b1, const T* st, T* y, cudaStream_t s) {
+  static bool init = false;
+  const size_t smem = sizeof(T) * diag_smem_words<P>();
+  if (!init) {
+    cudaError_t e = set_smem(diag_kernel<P, T>, smem);
+    if (e != cudaSuccess) return e;
+    init = true;
+  }
+  auto prm = make_params<T, P>(h, b1);
+  diag_kernel<P, T><<<h.nelem, elem_threads(P), smem, s>>>(prm, st, y);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_mass(const HostElemData& h, const double* x, double* y, cudaStream_t s) {
+  static bool init = false;
+  const size_t smem = sizeof(double) * elem_smem_words<P>();
+  if (!init) {
+    cudaError_t e = set_smem(mass_kernel<P, double>, smem);
+    if (e != cudaSuccess) return e;
+    init = true;
+  }
+  auto prm = make_params<double, P>(h, 0.0);
+  mass_kernel<P, double><<<h.nelem, elem_threads(P), smem, s>>>(prm, x, y);
+  return cudaGetLastError();
+}
+
+#define SDME_INSTANTIATE_ORDER(P)                                                                     \
+  template cudaError_t launch_residual<P>(const HostElemData&, double, const double*, double*, double*, \
+                                          float*, int*, cudaStream_t);                                \
+  template cudaError_t launch_tangent<P, double, double>(const HostElemData&, double, const double*,   \
+                                                         double*, const double*, double*, PcgScalars*, \
+                                                         cudaStream_t);                               \
+  template cudaError_t launch_tangent<P, float, double>(const HostElemData&, double, const double*,    \
+                                                        double*, const float*, double*, PcgScalars*,   \
+                                                        cudaStream_t);                                \
+  template cudaError_t launch_tangent<P, float, float>(const HostElemData&, double, const float*,      \
+                                                       float*, const float*, double*, PcgScalars*,     \
+                                                       cudaStream_t);                                 \
+  template cudaError_t launch_diag<P, double>(const HostElemData&, double, const double*, double*,     \
+                                              cudaStream_t);                                          \
+  template cudaError_t launch_diag<P, float>(const HostElemData&, double, const float*, float*,        \
+                                             cudaStream_t);                                           \
+  template cudaError_t launch_mass<P>(const HostElemData&, const double*, double*, cudaStream_t);
+
+}  // namespace sdme

@@ -1,0 +1,39 @@
+// Declarations of the per-order element-kernel launchers (no device code).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace sdme {
+
+struct PcgScalars;
+
+// Everything an element kernel needs, in float64 on the host; each launcher
+// converts it into its kernel-parameter block.
+struct HostElemData {
+  int P = 0;
+  int nelem = 0;
+  std::vector<double> B, D, DQ, W;   // Q x n, Q x n, Q x Q, Q (lattice order)
+  double s[3] = {0, 0, 0};           // 2 / h_d
+  double detJ = 0;
+  double mu = 0, lam = 0, rho = 0;
+  int ne[3] = {0, 0, 0};
+  int N[3] = {0, 0, 0};
+  int64_t Nn = 0;
+  unsigned clamp[6] = {0, 0, 0, 0, 0, 0};
+};
+
+template <int P>
+cudaError_t launch_residual(const HostElemData& h, double b1, const double* u, double* y, double* st64,
+                            float* st32, int* err, cudaStream_t s);
+template <int P, typename T, typename TV>
+cudaError_t launch_tangent(const HostElemData& h, double b1, const TV* x, TV* y, const T* st,
+                           double* partial, PcgScalars* scal, cudaStream_t s);
+template <int P, typename T>
+cudaError_t launch_diag(const HostElemData& h, double b1, const T* st, T* y, cudaStream_t s);
+template <int P>
+cudaError_t launch_mass(const HostElemData& h, const double* x, double* y, cudaStream_t s);
+
+}  // namespace sdme

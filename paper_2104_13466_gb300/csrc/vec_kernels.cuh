@@ -1,0 +1,228 @@
+// Per-DOF kernels: Dirichlet handling, Newton residual assembly, Newmark
+// updates and the fused Jacobi-PCG vector steps.  Grid-stride loops over a
+// fixed grid (a multiple of the SM count); float64 reductions finished by the
+// last CTA to arrive (deterministic order, no waiting).
+#pragma once
+
+#include "common.cuh"
+
+namespace sdme {
+
+constexpr int kVecThreads = 256;
+
+// y = x on constrained DOFs, 0 elsewhere (start of a masked operator apply).
+template <typename TV>
+__global__ void __launch_bounds__(kVecThreads) k_mask_init(MeshInfo mi, const TV* __restrict__ x,
+                                                           TV* __restrict__ y) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
+       g += (int64_t)gridDim.x * blockDim.x)
+    y[g] = dof_constrained(mi, g) ? x[g] : TV(0);
+}
+
+// Diagonal post-processing: constrained -> 1; out = inverse ? 1/d : d.
+template <typename TV>
+__global__ void __launch_bounds__(kVecThreads) k_diag_finish(MeshInfo mi, TV* __restrict__ d, int inverse) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    TV v = dof_constrained(mi, g) ? TV(1) : d[g];
+    d[g] = inverse ? TV(1) / v : v;
+  }
+}
+
+// psi = P + mhat - y (mhat may be null), 0 on constrained DOFs; out = ||psi||^2.
+__global__ void __launch_bounds__(kVecThreads) k_residual_combine(MeshInfo mi, const double* __restrict__ Pl,
+                                                                  const double* __restrict__ mhat,
+                                                                  const double* __restrict__ y,
+                                                                  double* __restrict__ psi,
+                                                                  double* __restrict__ partial,
+                                                                  unsigned int* counter, double* out) {
+  double s = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (!dof_constrained(mi, g)) {
+      v = (Pl ? Pl[g] : 0.0) - y[g];
+      if (mhat) v += mhat[g];
+    }
+    psi[g] = v;
+    s += v * v;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  if (last_block_done(counter)) {
+    const double t = ordered_sum(partial, gridDim.x);
+    if (threadIdx.x == 0) {
+      *out = t;
+      *counter = 0;
+    }
+  }
+}
+
+// out = ||x||^2 (all DOFs)
+__global__ void __launch_bounds__(kVecThreads) k_norm2(int64_t n, const double* __restrict__ x,
+                                                       double* __restrict__ partial, unsigned int* counter,
+                                                       double* out) {
+  double s = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    s += x[g] * x[g];
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  if (last_block_done(counter)) {
+    const double t = ordered_sum(partial, gridDim.x);
+    if (threadIdx.x == 0) {
+      *out = t;
+      *counter = 0;
+    }
+  }
+}
+
+// ahat = b2 v + b3 a + b1 u_n, so that a(u) = b1 u - ahat (Newmark, Sec. 4.2)
+__global__ void __launch_bounds__(kVecThreads) k_newmark_ahat(int64_t n, const double* __restrict__ un,
+                                                              const double* __restrict__ v,
+                                                              const double* __restrict__ a, double b1, double b2,
+                                                              double b3, double* __restrict__ ahat) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    ahat[g] = b2 * v[g] + b3 * a[g] + b1 * un[g];
+}
+
+// a_{n+1} = b1 u - ahat ; v_{n+1} = v_n + dt ((1 - gamma) a_n + gamma a_{n+1})
+__global__ void __launch_bounds__(kVecThreads) k_newmark_final(int64_t n, const double* __restrict__ u,
+                                                               const double* __restrict__ ahat, double b1,
+                                                               double dt, double gamma, double* __restrict__ v,
+                                                               double* __restrict__ a) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const double an = a[g];
+    const double a1 = b1 * u[g] - ahat[g];
+    v[g] = v[g] + dt * ((1.0 - gamma) * an + gamma * a1);
+    a[g] = a1;
+  }
+}
+
+// y += alpha x, x given in TV (converted to float64)
+template <typename TV>
+__global__ void __launch_bounds__(kVecThreads) k_axpy(int64_t n, double alpha, const TV* __restrict__ x,
+                                                      double* __restrict__ y) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    y[g] += alpha * (double)x[g];
+}
+
+//----------------------------------------------------------------------------
+// Jacobi PCG (CGD).  Vectors in TV; dinv = 1 / diag.
+//   init:      r = scale*b (0 on constrained), x = 0, q = 0, p = z = dinv r,
+//              rz = r.z, bb = r.r
+//   per iteration:  tangent kernel: q = A p, pq = p.q, alpha = rz / pq
+//                   update:    x += alpha p, r -= alpha q, q = 0,
+//                              rz' = r.(dinv r), rr = r.r, test, beta = rz'/rz
+//                   direction: p = dinv r + beta p
+// Per-thread partial sums run in TV; reductions across threads in float64.
+//----------------------------------------------------------------------------
+template <typename TV>
+__global__ void __launch_bounds__(kVecThreads) k_pcg_init(MeshInfo mi, const double* __restrict__ b, double scale,
+                                                          const TV* __restrict__ dinv, TV* __restrict__ x,
+                                                          TV* __restrict__ r, TV* __restrict__ p,
+                                                          TV* __restrict__ q, PcgScalars* scal,
+                                                          double* __restrict__ partial, double rtol, int maxit) {
+  TV srz = TV(0), srr = TV(0);
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const TV rv = dof_constrained(mi, g) ? TV(0) : (TV)(scale * b[g]);
+    const TV z = dinv[g] * rv;
+    r[g] = rv;
+    p[g] = z;
+    x[g] = TV(0);
+    q[g] = TV(0);
+    srz += rv * z;
+    srr += rv * rv;
+  }
+  double a = (double)srz, c = (double)srr;
+  block_sum2(a, c);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = a;
+    partial[2 * blockIdx.x + 1] = c;
+  }
+  if (last_block_done(&scal->counter2)) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+      s0 += ((volatile double*)partial)[2 * i];
+      s1 += ((volatile double*)partial)[2 * i + 1];
+    }
+    block_sum2(s0, s1);
+    if (threadIdx.x == 0) {
+      scal->rz = s0;
+      scal->bb = s1;
+      scal->rr = s1;
+      scal->tol2 = rtol * rtol * s1;
+      scal->iter = 0;
+      scal->maxit = maxit;
+      scal->alpha = 0.0;
+      scal->beta = 0.0;
+      scal->pq = 0.0;
+      scal->status = (s1 == 0.0) ? kPcgConverged : (isfinite(s1) ? kPcgRunning : kPcgBreakdown);
+      scal->counter = 0;
+      scal->counter2 = 0;
+    }
+  }
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TV* __restrict__ x, TV* __restrict__ r,
+                                                            const TV* __restrict__ p, TV* __restrict__ q,
+                                                            const TV* __restrict__ dinv, PcgScalars* scal,
+                                                            double* __restrict__ partial) {
+  if (scal->status != kPcgRunning) return;
+  const TV alpha = (TV)scal->alpha;
+  TV srz = TV(0), srr = TV(0);
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    const TV qv = q[g];
+    x[g] += alpha * p[g];
+    const TV rv = r[g] - alpha * qv;
+    r[g] = rv;
+    q[g] = TV(0);
+    srz += rv * (dinv[g] * rv);
+    srr += rv * rv;
+  }
+  double a = (double)srz, c = (double)srr;
+  block_sum2(a, c);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = a;
+    partial[2 * blockIdx.x + 1] = c;
+  }
+  if (last_block_done(&scal->counter2)) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+      s0 += ((volatile double*)partial)[2 * i];
+      s1 += ((volatile double*)partial)[2 * i + 1];
+    }
+    block_sum2(s0, s1);
+    if (threadIdx.x == 0) {
+      scal->iter += 1;
+      scal->rr = s1;
+      scal->beta = s0 / scal->rz;
+      scal->rz = s0;
+      if (!isfinite(s1) || !isfinite(s0)) scal->status = kPcgBreakdown;
+      else if (s1 <= scal->tol2) scal->status = kPcgConverged;
+      else if (scal->iter >= scal->maxit) scal->status = kPcgMaxit;
+      scal->counter2 = 0;
+    }
+  }
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(kVecThreads) k_pcg_direction(int64_t n, const TV* __restrict__ r,
+                                                               const TV* __restrict__ dinv, TV* __restrict__ p,
+                                                               const PcgScalars* scal) {
+  if (scal->status != kPcgRunning) return;
+  const TV beta = (TV)scal->beta;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    p[g] = dinv[g] * r[g] + beta * p[g];
+}
+
+// out = scale * x (TV -> float64)
+template <typename TV>
+__global__ void __launch_bounds__(kVecThreads) k_to_double(int64_t n, const TV* __restrict__ x, double scale,
+                                                           double* __restrict__ out) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    out[g] = scale * (double)x[g];
+}
+
+}  // namespace sdme
