@@ -68,7 +68,7 @@ class Timing(ctypes.Structure):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError("libsdme.so not built at %s; run `python -m paper_2104_13466_gb300.build` "
+        raise ImportError("libsdme.so not built at %s; run `python paper_2104_13466_gb300/build.py` "
                           "(there is no CPU fallback)" % LIB_PATH)
     lib = ctypes.CDLL(LIB_PATH)
     for name in EXPORTS:

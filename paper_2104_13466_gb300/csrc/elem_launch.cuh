@@ -32,11 +32,12 @@ static ElemParams<T, P> make_params(const HostElemData& h, double b1) {
   return p;
 }
 
+// Opt in to the dynamic shared memory the kernel needs.  Always set: the
+// 48 KB default counts static shared memory too (the reduction buffers), so
+// a dynamic size just under 48 KB can already fail without it.
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024)
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <int P>

@@ -21,8 +21,8 @@ def _declared():
 @pytest.fixture(scope="module")
 def lib():
     if not os.path.exists(LIB):
-        from paper_2104_13466_gb300 import build
-        build.build(verbose=False)
+        import __graft_entry__
+        __graft_entry__._build_module().build(verbose=False)
     return ctypes.CDLL(LIB)
 
 
