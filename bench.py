@@ -307,6 +307,31 @@ def run_gpu(args, w):
         torch.distributed.destroy_process_group()
 
 
+def run_kernel_only(args, w):
+    """A few PCG iterations at the full bench size: linearise at a seeded
+    displacement, then run ``--kernel-iters`` iterations (rtol 0), timing
+    every tangent launch with CUDA events.  Used for kernel profiles."""
+    import torch
+    import paper_2104_13466_gb300 as sd
+    from synthetic import random_vector
+    prec = sd.MIXED_FP32 if args.precision == "mixed" else sd.FP64
+    mu, lam = lame(w["E"], w["nu"])
+    ctx = sd.Context(w["elems"], w["lengths"], w["clamp"], mu, lam, w["rho"], w["P"], args.basis, precision=prec)
+    n = ctx.ndof
+    u = torch.from_numpy(random_vector(n, 1, 1e-4)).cuda()
+    b = torch.from_numpy(random_vector(n, 2)).cuda()
+    x = torch.zeros_like(u)
+    ctx.set_timing(True)
+    its, rel = ctx.pcg_solve(u, 4.0, b, x, rtol=0.0, maxit=args.kernel_iters, allow_maxit=True)
+    t = ctx.timing()
+    avg = t["tangent_ms"] / max(1, t["tangent_launches"])
+    flops = tangent_flops_per_element(w["P"]) * ctx.nelem
+    print(json.dumps({"mode": "kernel-only", "precision": args.precision, "basis": args.basis, "iters": its,
+                      "tangent_avg_ms": avg, "tflops": flops / (avg * 1e-3) / 1e12, "launches": t["tangent_launches"]}),
+          flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -322,9 +347,13 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--ref-sample", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-only", action="store_true")
+    ap.add_argument("--kernel-iters", type=int, default=20)
     args = ap.parse_args()
     w = workload(args.workload)
-    if args.impl == "reference":
+    if args.kernel_only:
+        run_kernel_only(args, w)
+    elif args.impl == "reference":
         run_reference(args, w)
     else:
         run_gpu(args, w)
