@@ -220,6 +220,38 @@ typedef struct {
 sdme_status sdme_set_timing(sdme_ctx* ctx, int enable);
 sdme_status sdme_get_timing(sdme_ctx* ctx, sdme_timing* out);
 
+/*
+ * y_dev = (b1 M + K_T(u)) x_dev in float64, like sdme_tangent_apply, but
+ * without a context and without allocating anything: no cudaMalloc,
+ * cudaFree, host heap or library allocation.  The paper has no counterpart;
+ * this exists for callers that cannot allocate device memory, such as code
+ * running under a fixed memory budget or a pool that forbids new device
+ * allocations, or while other work must not be disturbed by allocator
+ * synchronisation.
+ *
+ * Inputs: mesh, material and order P (1..8) as for sdme_create; the 1D
+ * tables xq[Q], wq[Q], B[Q*(P+1)], D[Q*(P+1)] with Q = P + 2, exactly as
+ * sdme_build_basis1d returns them (host arrays, read during the call);
+ * u_dev (linearisation point), x_dev, y_dev: float64 device vectors of
+ * length 3 Nn.  Constrained DOFs get y = x, as in sdme_tangent_apply.
+ *
+ * Scratch: the linearisation state and the discarded internal-force vector
+ * live in one static device array of 2^21 float64 words (16 MiB) that every
+ * GPU loading the library holds until the process exits.  A call needs
+ * 32 + 3 Nn + 10 (P+2)^3 nelem words; larger problems return SDME_EINVAL.
+ * The array is shared by all calls and keeps the last call's contents; the
+ * call clears what must start at zero.  Calls that overlap on the GPU (for
+ * example on two streams at once) race on the array and must be avoided.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  The call synchronises `stream` (NULL = legacy
+ * default stream) to report SDME_NONPOSITIVE_J.
+ */
+sdme_status sdme_tangent_apply_noalloc(const sdme_mesh_desc* mesh, const sdme_material* mat, int P,
+                                       const double* xq, const double* wq, const double* B, const double* D,
+                                       const double* u_dev, double b1, const double* x_dev, double* y_dev,
+                                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

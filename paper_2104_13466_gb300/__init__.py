@@ -29,7 +29,8 @@ FACE_NAMES = {"xmin": XMIN, "xmax": XMAX, "ymin": YMIN, "ymax": YMAX, "zmin": ZM
 
 EXPORTS = ("sdme_status_string", "sdme_build_basis1d", "sdme_create", "sdme_destroy", "sdme_get_sizes",
            "sdme_internal_force", "sdme_mass_apply", "sdme_tangent_apply", "sdme_diagonal", "sdme_pcg_solve",
-           "sdme_traction_load", "sdme_implicit_newmark_step", "sdme_set_timing", "sdme_get_timing")
+           "sdme_traction_load", "sdme_implicit_newmark_step", "sdme_set_timing", "sdme_get_timing",
+           "sdme_tangent_apply_noalloc")
 
 
 class BasisDesc(ctypes.Structure):
@@ -93,6 +94,8 @@ def _load():
                                                ctypes.POINTER(StepStats)]
     lib.sdme_set_timing.argtypes = [vp, i]
     lib.sdme_get_timing.argtypes = [vp, ctypes.POINTER(Timing)]
+    lib.sdme_tangent_apply_noalloc.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(Material), i, pd, pd, pd,
+                                               pd, vp, d, vp, vp, vp]
     for name in EXPORTS:
         if name != "sdme_status_string":
             getattr(lib, name).restype = ctypes.c_int
@@ -153,6 +156,22 @@ def mesh_desc(elems, lengths, clamp):
             bits |= 1 << int(c)
         m.clamp[FACE_NAMES[f] if isinstance(f, str) else int(f)] = bits
     return m
+
+
+def tangent_apply_noalloc(elems, lengths, clamp, mu, lam, rho, P, tables, u, b1, x, y, stream=None):
+    """sdme_tangent_apply_noalloc: float64 tangent matvec without a context
+    and without any allocation; ``tables`` = (xq, wq, B, D) as returned by
+    build_basis1d (float64 numpy arrays)."""
+    import numpy as np
+    import torch
+    mesh = mesh_desc(elems, lengths, clamp)
+    mat = Material(float(mu), float(lam), float(rho))
+    arrs = [np.ascontiguousarray(t, dtype=np.float64) for t in tables]
+    ptrs = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs]
+    stream = stream or torch.cuda.current_stream()
+    return _check(lib.sdme_tangent_apply_noalloc(ctypes.byref(mesh), ctypes.byref(mat), int(P), *ptrs, _ptr(u),
+                                                 float(b1), _ptr(x), _ptr(y), ctypes.c_void_p(stream.cuda_stream)),
+                  "sdme_tangent_apply_noalloc")
 
 
 class Context:
