@@ -73,6 +73,26 @@ __device__ __forceinline__ double block_sum(double v) {
   return out_;
 }
 
+// Sum over the CTA in the given type; result valid in every thread.
+template <typename T>
+__device__ __forceinline__ T block_sum_t(T v) {
+  __shared__ T red_t_[32];
+  __shared__ T out_t_;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red_t_[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    T w = (threadIdx.x < ((blockDim.x + 31) >> 5)) ? red_t_[threadIdx.x] : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) out_t_ = w;
+  }
+  __syncthreads();
+  return out_t_;
+}
+
 // Two sums at once.
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
   __shared__ double ra_[32], rb_[32];

@@ -56,91 +56,6 @@ __device__ __forceinline__ bool is_constrained(const Prm& p, int c, int ix, int 
          ((iz == 0) && (p.clamp[4] & bit)) || ((iz == p.N[2] - 1) && (p.clamp[5] & bit));
 }
 
-// Contract a set of 3D arrays along one axis, one thread per line.
-// Arrays are [d2][d1][d0] (d0 fastest); a line runs along the contracted
-// axis, whose extent goes NI -> NO.  `outer` = product of the extents before
-// the axis, `inner` = product after it (stride of the axis).  Fields are
-// `sfs` / `dfs` words apart.  Matrix: !TR: out[o] = sum_i M[o*NI + i] in[i];
-// TR: out[o] = sum_i M[i*NO + o] in[i].  ACC adds into dst.
-template <int NI, int NO, bool TR, bool ACC, typename T>
-__device__ __forceinline__ void contract(const T* __restrict__ src, T* __restrict__ dst,
-                                         const T* __restrict__ M, int nfields, int outer, int inner,
-                                         int sfs, int dfs) {
-  const int per_field = outer * inner;
-  const int total = nfields * per_field;
-  for (int l = threadIdx.x; l < total; l += blockDim.x) {
-    const int f = l / per_field;
-    const int rem = l - f * per_field;
-    const int o = rem / inner;
-    const int i = rem - o * inner;
-    const T* s = src + f * sfs + o * NI * inner + i;
-    T* d = dst + f * dfs + o * NO * inner + i;
-    T in[NI];
-#pragma unroll
-    for (int a = 0; a < NI; ++a) in[a] = s[a * inner];
-#pragma unroll
-    for (int b = 0; b < NO; ++b) {
-      T acc = ACC ? d[b * inner] : T(0);
-#pragma unroll
-      for (int a = 0; a < NI; ++a) acc += (TR ? M[a * NO + b] : M[b * NI + a]) * in[a];
-      d[b * inner] = acc;
-    }
-  }
-}
-
-// Forward: X[3][n^3] (in Gb region) -> U[3][Q^3] values.  Buffers:
-// S1 = [3][n][n][Q], S2 = [3][n][Q][Q], placed after X inside Gb.
-template <typename T, int P>
-__device__ __forceinline__ void interp_forward(const ElemTables<T, P>& tb, T* X, T* U, T* Gb) {
-  constexpr int n = P + 1, Q = P + 2;
-  T* S1 = Gb + 3 * n * n * n;
-  T* S2 = S1 + 3 * n * n * Q;
-  contract<n, Q, false, false>(X, S1, tb.B, 3, n * n, 1, n * n * n, n * n * Q);
-  __syncthreads();
-  contract<n, Q, false, false>(S1, S2, tb.B, 3, n, Q, n * n * Q, n * Q * Q);
-  __syncthreads();
-  contract<n, Q, false, false>(S2, U, tb.B, 3, 1, Q * Q, n * Q * Q, Q * Q * Q);
-  __syncthreads();
-}
-
-// Collocated reference derivatives: G[(c*3+d)][Q^3] = d/dxi_d U_c.
-template <typename T, int P>
-__device__ __forceinline__ void derivs_forward(const ElemTables<T, P>& tb, const T* U, T* G) {
-  constexpr int Q = P + 2, Q3 = Q * Q * Q;
-  contract<Q, Q, false, false>(U, G + 0 * Q3, tb.DQ, 3, Q * Q, 1, Q3, 3 * Q3);
-  contract<Q, Q, false, false>(U, G + 1 * Q3, tb.DQ, 3, Q, Q, Q3, 3 * Q3);
-  contract<Q, Q, false, false>(U, G + 2 * Q3, tb.DQ, 3, 1, Q * Q, Q3, 3 * Q3);
-  __syncthreads();
-}
-
-// Transposed derivatives accumulated into the value fluxes:
-// U_c += sum_d DQ_d^T G_cd.
-template <typename T, int P>
-__device__ __forceinline__ void derivs_transpose(const ElemTables<T, P>& tb, const T* G, T* U) {
-  constexpr int Q = P + 2, Q3 = Q * Q * Q;
-  contract<Q, Q, true, true>(G + 0 * Q3, U, tb.DQ, 3, Q * Q, 1, 3 * Q3, Q3);
-  __syncthreads();
-  contract<Q, Q, true, true>(G + 1 * Q3, U, tb.DQ, 3, Q, Q, 3 * Q3, Q3);
-  __syncthreads();
-  contract<Q, Q, true, true>(G + 2 * Q3, U, tb.DQ, 3, 1, Q * Q, 3 * Q3, Q3);
-  __syncthreads();
-}
-
-// Transposed interpolation U[3][Q^3] -> Y[3][n^3] (Y at the start of Gb).
-template <typename T, int P>
-__device__ __forceinline__ void interp_transpose(const ElemTables<T, P>& tb, const T* U, T* Gb) {
-  constexpr int n = P + 1, Q = P + 2;
-  T* Y = Gb;
-  T* S1 = Gb + 3 * n * n * n;
-  T* S2 = S1 + 3 * n * n * Q;
-  contract<Q, n, true, false>(U, S2, tb.B, 3, 1, Q * Q, Q * Q * Q, n * Q * Q);
-  __syncthreads();
-  contract<Q, n, true, false>(S2, S1, tb.B, 3, n, Q, n * Q * Q, n * n * Q);
-  __syncthreads();
-  contract<Q, n, true, false>(S1, Y, tb.B, 3, n * n, 1, n * n * Q, n * n * n);
-  __syncthreads();
-}
-
 template <typename T>
 __device__ __forceinline__ double to_double(T v) { return static_cast<double>(v); }
 
@@ -165,17 +80,236 @@ __device__ __forceinline__ T wprod(const T* W, int q, int Q) {
   return W[k1] * W[k2] * W[k3];
 }
 
+// Shared-memory geometry of the element kernels for order P.  Arrays are
+// [component][z][y][x] with the x extent padded to an odd pitch so that
+// threads walking consecutive lines hit distinct banks.
+template <int P>
+struct Geo {
+  static constexpr int n = P + 1, Q = P + 2;
+  static constexpr int XQ = Q | 1;             // pitch of an x extent Q
+  static constexpr int XN = n | 1;             // pitch of an x extent n
+  static constexpr int FQ = Q * Q * XQ;        // one component of a Q^3 field
+  static constexpr int SX = n * n * XN;        // one component of X [n][n][n]
+  static constexpr int SA1 = n * n * XQ;       // [n][n][Q]
+  static constexpr int SA2 = n * Q * XQ;       // [n][Q][Q]
+  static constexpr int NT = (3 * Q * Q + 31) / 32 * 32;   // one thread per (component, line)
+  static constexpr int WORDS = 12 * FQ;        // U, Gx, Gy, Gz
+};
+
 // Number of threads per CTA for order P.
-__host__ __device__ constexpr int elem_threads(int P) {
-  return ((P + 2) * (P + 2) * (P + 2) + 31) / 32 * 32 > 512 ? 512
-                                                            : ((P + 2) * (P + 2) * (P + 2) + 31) / 32 * 32;
-}
+__host__ __device__ constexpr int elem_threads(int P) { return (3 * (P + 2) * (P + 2) + 31) / 32 * 32; }
 
 template <int P>
 constexpr int elem_smem_words() {
-  return 12 * (P + 2) * (P + 2) * (P + 2);
+  return Geo<P>::WORDS;
 }
 
+// One line contraction: out[b] (+)= sum_a M(b, a) in[a] with
+// M(b, a) = TR ? Mt[a*NO + b] : Mt[b*NI + a]; source / destination element
+// strides si / so.
+template <int NI, int NO, bool TR, bool ACC, typename T>
+__device__ __forceinline__ void line1(const T* __restrict__ Mt, const T* s, int si, T* d, int so) {
+  T in[NI];
+#pragma unroll
+  for (int a = 0; a < NI; ++a) in[a] = s[a * si];
+#pragma unroll
+  for (int b = 0; b < NO; ++b) {
+    T acc = ACC ? d[b * so] : T(0);
+#pragma unroll
+    for (int a = 0; a < NI; ++a) acc += (TR ? Mt[a * NO + b] : Mt[b * NI + a]) * in[a];
+    d[b * so] = acc;
+  }
+}
+
+// Forward stages.  On entry X [3][n][n][XN] (in region 1) holds the element
+// coefficients; on exit U [3][Q^3] (region 0) holds values at the Gauss
+// points and, if GRAD, Gx, Gy, Gz (regions 1, 2, 3) the reference
+// derivatives d/dxi_d.  One thread per (component, line) in every stage:
+//   F1 x-interpolation  X  -> A1 [3][n][n][Q] (region 2)
+//   F2 y-interpolation  A1 -> A2 [3][n][Q][Q] (region 1)
+//   F3 z-interpolation  A2 -> U, with the z-derivative of the same column
+//      taken in registers (collocation matrix DQ)
+//   D  x- and y-derivatives of U.
+template <typename T, int P, bool GRAD>
+__device__ __forceinline__ void forward_stages(const ElemTables<T, P>& tb, T* sm) {
+  using G = Geo<P>;
+  constexpr int n = G::n, Q = G::Q, XQ = G::XQ, XN = G::XN, FQ = G::FQ;
+  T* U = sm;
+  T* R1 = sm + 3 * FQ;
+  T* R2 = sm + 6 * FQ;
+  T* R3 = sm + 9 * FQ;
+  const int t = threadIdx.x;
+  {  // F1: lines (c, r, q)
+    constexpr int L = n * n;
+    if (t < 3 * L) {
+      const int c = t / L, l = t - c * L;
+      line1<n, Q, false, false>(tb.B, R1 + c * G::SX + l * XN, 1, R2 + c * G::SA1 + l * XQ, 1);
+    }
+  }
+  __syncthreads();
+  {  // F2: lines (c, r, qx)
+    constexpr int L = n * Q;
+    if (t < 3 * L) {
+      const int c = t / L, l = t - c * L, r = l / Q, qx = l - r * Q;
+      line1<n, Q, false, false>(tb.B, R2 + c * G::SA1 + r * n * XQ + qx, XQ, R1 + c * G::SA2 + r * Q * XQ + qx,
+                                XQ);
+    }
+  }
+  __syncthreads();
+  {  // F3 (+ z-derivative): lines (c, qy, qx)
+    constexpr int L = Q * Q;
+    if (t < 3 * L) {
+      const int c = t / L, l = t - c * L, qy = l / Q, qx = l - qy * Q;
+      const T* s = R1 + c * G::SA2 + qy * XQ + qx;
+      T in[n];
+#pragma unroll
+      for (int a = 0; a < n; ++a) in[a] = s[a * Q * XQ];
+      T u[Q];
+#pragma unroll
+      for (int b = 0; b < Q; ++b) {
+        T acc = T(0);
+#pragma unroll
+        for (int a = 0; a < n; ++a) acc += tb.B[b * n + a] * in[a];
+        u[b] = acc;
+      }
+      const int o = c * FQ + qy * XQ + qx;
+#pragma unroll
+      for (int b = 0; b < Q; ++b) U[o + b * Q * XQ] = u[b];
+      if (GRAD) {
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+          T acc = T(0);
+#pragma unroll
+          for (int m = 0; m < Q; ++m) acc += tb.DQ[b * Q + m] * u[m];
+          R3[o + b * Q * XQ] = acc;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (GRAD) {
+    constexpr int L = Q * Q;
+    if (t < 3 * L) {
+      const int c = t / L, l = t - c * L, hi = l / Q, lo = l - hi * Q;
+      // x-lines at (qz = hi, qy = lo)
+      line1<Q, Q, false, false>(tb.DQ, U + c * FQ + l * XQ, 1, R1 + c * FQ + l * XQ, 1);
+      // y-lines at (qz = hi, qx = lo)
+      line1<Q, Q, false, false>(tb.DQ, U + c * FQ + hi * Q * XQ + lo, XQ, R2 + c * FQ + hi * Q * XQ + lo, XQ);
+    }
+    __syncthreads();
+  }
+}
+
+// Transposed stages.  On entry U holds the value fluxes and (if GRAD) Gx,
+// Gy, Gz the stress fluxes at the Gauss points; on exit Y [3][n][n][XN]
+// (region 1) holds the element result.
+//   DTx, DTy  U += DQ^T along x, then along y
+//   T3        z-lines: w = U + DQ^T Gz, then B^T w -> A2' [3][n][Q][Q] (region 1)
+//   T2        y: A2' -> A1' [3][n][n][Q] (region 2)
+//   T1        x: A1' -> Y (region 1)
+template <typename T, int P, bool GRAD>
+__device__ __forceinline__ void transpose_stages(const ElemTables<T, P>& tb, T* sm) {
+  using G = Geo<P>;
+  constexpr int n = G::n, Q = G::Q, XQ = G::XQ, XN = G::XN, FQ = G::FQ;
+  T* U = sm;
+  T* R1 = sm + 3 * FQ;
+  T* R2 = sm + 6 * FQ;
+  T* R3 = sm + 9 * FQ;
+  const int t = threadIdx.x;
+  if (GRAD) {
+    constexpr int L = Q * Q;
+    if (t < 3 * L) {  // DTx: x-lines at (c, qz, qy)
+      const int c = t / L, l = t - c * L;
+      line1<Q, Q, true, true>(tb.DQ, R1 + c * FQ + l * XQ, 1, U + c * FQ + l * XQ, 1);
+    }
+    __syncthreads();
+    if (t < 3 * L) {  // DTy: y-lines at (c, qz, qx)
+      const int c = t / L, l = t - c * L, qz = l / Q, qx = l - qz * Q;
+      line1<Q, Q, true, true>(tb.DQ, R2 + c * FQ + qz * Q * XQ + qx, XQ, U + c * FQ + qz * Q * XQ + qx, XQ);
+    }
+    __syncthreads();
+  }
+  {  // T3 (+ transposed z-derivative): z-lines at (c, qy, qx)
+    constexpr int L = Q * Q;
+    if (t < 3 * L) {
+      const int c = t / L, l = t - c * L, qy = l / Q, qx = l - qy * Q;
+      const int o = c * FQ + qy * XQ + qx;
+      T w[Q];
+#pragma unroll
+      for (int a = 0; a < Q; ++a) w[a] = U[o + a * Q * XQ];
+      if (GRAD) {
+        T g[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) g[a] = R3[o + a * Q * XQ];
+#pragma unroll
+        for (int b = 0; b < Q; ++b) {
+          T acc = w[b];
+#pragma unroll
+          for (int a = 0; a < Q; ++a) acc += tb.DQ[a * Q + b] * g[a];
+          w[b] = acc;
+        }
+      }
+      T* d = R1 + c * G::SA2 + qy * XQ + qx;
+#pragma unroll
+      for (int p = 0; p < n; ++p) {
+        T acc = T(0);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) acc += tb.B[a * n + p] * w[a];
+        d[p * Q * XQ] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  {  // T2: lines (c, r, qx)
+    constexpr int L = n * Q;
+    if (t < 3 * L) {
+      const int c = t / L, l = t - c * L, r = l / Q, qx = l - r * Q;
+      line1<Q, n, true, false>(tb.B, R1 + c * G::SA2 + r * Q * XQ + qx, XQ, R2 + c * G::SA1 + r * n * XQ + qx, XQ);
+    }
+  }
+  __syncthreads();
+  {  // T1: lines (c, r, q)
+    constexpr int L = n * n;
+    if (t < 3 * L) {
+      const int c = t / L, l = t - c * L;
+      line1<Q, n, true, false>(tb.B, R2 + c * G::SA1 + l * XQ, 1, R1 + c * G::SX + l * XN, 1);
+    }
+  }
+  __syncthreads();
+}
+
+// Per-element view of the global lattice for gather / scatter: the lattice
+// offset of local point (p, q, r) is base + (r N1 + q) N0 + p, and only
+// elements that touch a clamped face need the per-entry Dirichlet test.
+template <typename Prm>
+struct ElemView {
+  int64_t base;   // lattice index of local (0, 0, 0)
+  int ex, ey, ez;
+  bool boundary;  // touches a clamped face (any component)
+  __device__ __forceinline__ ElemView(const Prm& p, int P, int e) {
+    ex = e % p.ne[0];
+    ey = (e / p.ne[0]) % p.ne[1];
+    ez = e / (p.ne[0] * p.ne[1]);
+    base = ((int64_t)(ez * P) * p.N[1] + ey * P) * (int64_t)p.N[0] + ex * P;
+    boundary = (ex == 0 && p.clamp[0]) || (ex == p.ne[0] - 1 && p.clamp[1]) || (ey == 0 && p.clamp[2]) ||
+               (ey == p.ne[1] - 1 && p.clamp[3]) || (ez == 0 && p.clamp[4]) || (ez == p.ne[2] - 1 && p.clamp[5]);
+  }
+};
+
+// (c, m) entry idx of an element: global DOF index, constrained flag and
+// offset in the shared X / Y array.
+template <int P, typename Prm>
+__device__ __forceinline__ int64_t entry_index(const Prm& p, const ElemView<Prm>& v, int idx, bool* cons,
+                                               int* soff) {
+  using G = Geo<P>;
+  constexpr int n = G::n, n3 = n * n * n;
+  const int c = idx / n3, m = idx - c * n3;
+  const int rq = m / n, pp = m - rq * n;
+  const int r = rq / n, q = rq - r * n;
+  *soff = c * G::SX + rq * G::XN + pp;
+  *cons = v.boundary && is_constrained(p, c, v.ex * P + pp, v.ey * P + q, v.ez * P + r);
+  return c * p.Nn + v.base + ((int64_t)r * p.N[1] + q) * p.N[0] + pp;
+}
 
 //-----------------------------------------------------------------------------
 // Residual: y += R(u) + b1 M u, and the linearisation state at u.
@@ -188,28 +322,30 @@ residual_kernel(const __grid_constant__ ElemParams<double, P> prm, const double*
                 double* __restrict__ y, double* __restrict__ st64, float* __restrict__ st32,
                 int* __restrict__ err) {
   using T = double;
-  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q;
+  using G = Geo<P>;
+  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* U = reinterpret_cast<T*>(smem_raw);
-  T* G = U + 3 * Q3;
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* X = sm + 3 * FQ;
   const int e = blockIdx.x;
-  const int ex = e % prm.ne[0], ey = (e / prm.ne[0]) % prm.ne[1], ez = e / (prm.ne[0] * prm.ne[1]);
+  const ElemView<ElemParams<double, P>> view(prm, P, e);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
-    int64_t g = dof_index(prm, P, ex, ey, ez, idx, &cons);
-    G[idx] = u[g];
+    int so;
+    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
+    X[so] = u[g];
   }
   __syncthreads();
-  interp_forward<T, P>(prm.tab, G, U, G);
-  derivs_forward<T, P>(prm.tab, U, G);
-  const T s0 = prm.s[0], s1 = prm.s[1], s2 = prm.s[2];
-  const T sc[3] = {s0, s1, s2};
+  forward_stages<T, P, true>(prm.tab, sm);
+  const T sc[3] = {prm.s[0], prm.s[1], prm.s[2]};
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
+    const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
+    const int so = (qz * Q + qy) * XQ + qx;
     T F[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int d = 0; d < 3; ++d) F[c][d] = (c == d ? T(1) : T(0)) + G[(c * 3 + d) * Q3 + q] * sc[d];
+      for (int d = 0; d < 3; ++d) F[c][d] = (c == d ? T(1) : T(0)) + sm[(3 + 3 * d + c) * FQ + so] * sc[d];
     T cof[3][3];
     cof[0][0] = F[1][1] * F[2][2] - F[1][2] * F[2][1];
     cof[0][1] = F[1][2] * F[2][0] - F[1][0] * F[2][2];
@@ -224,7 +360,7 @@ residual_kernel(const __grid_constant__ ElemParams<double, P> prm, const double*
     if (!(J > T(0))) atomicOr(err, 1);
     const T iJ = T(1) / J;
     const T lnJ = log(J);
-    const T wdet = wprod(prm.tab.W, q, Q) * prm.detJ;
+    const T wdet = prm.tab.W[qx] * prm.tab.W[qy] * prm.tab.W[qz] * prm.detJ;
     const T a = prm.lam * lnJ;
     const T cst = prm.mu - a;
 #pragma unroll
@@ -233,65 +369,76 @@ residual_kernel(const __grid_constant__ ElemParams<double, P> prm, const double*
       for (int d = 0; d < 3; ++d) {
         const T H = cof[c][d] * iJ;  // (F^{-T})_cd
         const T Pcd = prm.mu * (F[c][d] - H) + a * H;
-        G[(c * 3 + d) * Q3 + q] = wdet * Pcd * sc[d];
-        const int64_t so = ((int64_t)e * kStateFields + (c * 3 + d)) * Q3 + q;
-        if (st64) st64[so] = H;
-        if (st32) st32[so] = (float)H;
+        sm[(3 + 3 * d + c) * FQ + so] = wdet * Pcd * sc[d];
+        const int64_t o = ((int64_t)e * kStateFields + (c * 3 + d)) * Q3 + q;
+        if (st64) st64[o] = H;
+        if (st32) st32[o] = (float)H;
       }
-    const int64_t so = ((int64_t)e * kStateFields + 9) * Q3 + q;
-    if (st64) st64[so] = cst;
-    if (st32) st32[so] = (float)cst;
+    const int64_t o = ((int64_t)e * kStateFields + 9) * Q3 + q;
+    if (st64) st64[o] = cst;
+    if (st32) st32[o] = (float)cst;
     const T mfac = prm.b1 * prm.rho * wdet;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) U[c * Q3 + q] *= mfac;
+    for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= mfac;
   }
   __syncthreads();
-  derivs_transpose<T, P>(prm.tab, G, U);
-  interp_transpose<T, P>(prm.tab, U, G);
+  transpose_stages<T, P, true>(prm.tab, sm);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
-    int64_t g = dof_index(prm, P, ex, ey, ez, idx, &cons);
-    atomicAdd(&y[g], G[idx]);
+    int so;
+    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
+    atomicAdd(&y[g], X[so]);
   }
 }
 
 //-----------------------------------------------------------------------------
 // Tangent: y += (b1 M + K_T(u)) x on free DOFs (x taken as 0 on constrained
-// DOFs), and dot_out[e] = x_e . (K_e x_e) for the PCG step length.
+// DOFs), and dot_partial[e] = x_e . (K_e x_e) for the PCG step length.
 // dP = mu dF + c F^{-T} dF^T F^{-T} + lambda (F^{-T} : dF) F^{-T}, c = mu - lambda ln J
 // (consistent linearisation of the first Piola stress, Sec. 3).
-// T: arithmetic type; TV: global vector type; TS: stored-state type.
+// T: arithmetic and stored-state type; TV: global vector type.
 //-----------------------------------------------------------------------------
+// Resident CTAs per SM the tangent kernel is register-budgeted for: its
+// shared memory (12 (P+2)^2 ((P+2)|1) words) allows four float32 or two
+// float64 element CTAs per SM at P = 8.
+template <typename T>
+constexpr int tangent_min_blocks() {
+  return sizeof(T) == 4 ? 4 : 2;
+}
+
 template <int P, typename T, typename TV>
-__global__ void __launch_bounds__(elem_threads(P))
+__global__ void __launch_bounds__(elem_threads(P), tangent_min_blocks<T>())
 tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restrict__ x,
                TV* __restrict__ y, const T* __restrict__ st, double* __restrict__ dot_partial,
                PcgScalars* __restrict__ scal) {
-  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q;
+  using G = Geo<P>;
+  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
   if (scal && scal->status != 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* U = reinterpret_cast<T*>(smem_raw);
-  T* G = U + 3 * Q3;
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* X = sm + 3 * FQ;
   const int e = blockIdx.x;
-  const int ex = e % prm.ne[0], ey = (e / prm.ne[0]) % prm.ne[1], ez = e / (prm.ne[0] * prm.ne[1]);
+  const ElemView<ElemParams<T, P>> view(prm, P, e);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
-    int64_t g = dof_index(prm, P, ex, ey, ez, idx, &cons);
-    G[idx] = cons ? T(0) : (T)x[g];
+    int so;
+    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
+    X[so] = cons ? T(0) : (T)x[g];
   }
   __syncthreads();
-  interp_forward<T, P>(prm.tab, G, U, G);
-  derivs_forward<T, P>(prm.tab, U, G);
+  forward_stages<T, P, true>(prm.tab, sm);
   const T sc[3] = {prm.s[0], prm.s[1], prm.s[2]};
   const T* ste = st + (int64_t)e * kStateFields * Q3;
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
+    const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
+    const int so = (qz * Q + qy) * XQ + qx;
     T H[3][3], dF[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         H[c][d] = ste[(c * 3 + d) * Q3 + q];
-        dF[c][d] = G[(c * 3 + d) * Q3 + q] * sc[d];
+        dF[c][d] = sm[(3 + 3 * d + c) * FQ + so] * sc[d];
       }
     const T cst = ste[9 * Q3 + q];
     T tr = T(0);
@@ -305,7 +452,7 @@ tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restric
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int j = 0; j < 3; ++j) W[a][j] = dF[0][a] * H[0][j] + dF[1][a] * H[1][j] + dF[2][a] * H[2][j];
-    const T wdet = wprod(prm.tab.W, q, Q) * prm.detJ;
+    const T wdet = prm.tab.W[qx] * prm.tab.W[qy] * prm.tab.W[qz] * prm.detJ;
     const T ltr = prm.lam * tr;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -313,30 +460,30 @@ tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restric
       for (int j = 0; j < 3; ++j) {
         const T V = H[i][0] * W[0][j] + H[i][1] * W[1][j] + H[i][2] * W[2][j];
         const T dP = prm.mu * dF[i][j] + cst * V + ltr * H[i][j];
-        G[(i * 3 + j) * Q3 + q] = wdet * dP * sc[j];
+        sm[(3 + 3 * j + i) * FQ + so] = wdet * dP * sc[j];
       }
     const T mfac = prm.b1 * prm.rho * wdet;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) U[c * Q3 + q] *= mfac;
+    for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= mfac;
   }
   __syncthreads();
-  derivs_transpose<T, P>(prm.tab, G, U);
-  interp_transpose<T, P>(prm.tab, U, G);
+  transpose_stages<T, P, true>(prm.tab, sm);
   T dotT = T(0);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
-    int64_t g = dof_index(prm, P, ex, ey, ez, idx, &cons);
+    int so;
+    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
     if (!cons) {
-      const T v = G[idx];
+      const T v = X[so];
       atomicAdd(&y[g], (TV)v);
       if (dot_partial) dotT += v * (T)x[g];
     }
   }
   if (dot_partial) {
     // x_e . (K_e x_e) summed over elements gives x . (K x) for the PCG step
-    // length; float64 across threads, fixed-order (deterministic) finalize
-    // by the last CTA to finish.
-    const double tot = block_sum(static_cast<double>(dotT));
+    // length; summed in T within the CTA, float64 across CTAs with a
+    // fixed-order (deterministic) finalize by the last CTA to finish.
+    const double tot = static_cast<double>(block_sum_t(dotT));
     if (threadIdx.x == 0) dot_partial[e] = tot;
     if (scal && last_block_done(&scal->counter)) {
       const double pq = ordered_sum(dot_partial, gridDim.x);
@@ -357,30 +504,35 @@ template <int P, typename T>
 __global__ void __launch_bounds__(elem_threads(P))
 mass_kernel(const __grid_constant__ ElemParams<T, P> prm, const double* __restrict__ x,
             double* __restrict__ y) {
-  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q;
+  using G = Geo<P>;
+  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* U = reinterpret_cast<T*>(smem_raw);
-  T* G = U + 3 * Q3;
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* X = sm + 3 * FQ;
   const int e = blockIdx.x;
-  const int ex = e % prm.ne[0], ey = (e / prm.ne[0]) % prm.ne[1], ez = e / (prm.ne[0] * prm.ne[1]);
+  const ElemView<ElemParams<T, P>> view(prm, P, e);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
-    int64_t g = dof_index(prm, P, ex, ey, ez, idx, &cons);
-    G[idx] = (T)x[g];
+    int so;
+    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
+    X[so] = (T)x[g];
   }
   __syncthreads();
-  interp_forward<T, P>(prm.tab, G, U, G);
+  forward_stages<T, P, false>(prm.tab, sm);
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
-    const T f = prm.rho * wprod(prm.tab.W, q, Q) * prm.detJ;
+    const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
+    const int so = (qz * Q + qy) * XQ + qx;
+    const T f = prm.rho * prm.tab.W[qx] * prm.tab.W[qy] * prm.tab.W[qz] * prm.detJ;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) U[c * Q3 + q] *= f;
+    for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= f;
   }
   __syncthreads();
-  interp_transpose<T, P>(prm.tab, U, G);
+  transpose_stages<T, P, false>(prm.tab, sm);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
-    int64_t g = dof_index(prm, P, ex, ey, ez, idx, &cons);
-    atomicAdd(&y[g], (double)G[idx]);
+    int so;
+    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
+    atomicAdd(&y[g], (double)X[so]);
   }
 }
 
