@@ -332,6 +332,53 @@ def run_kernel_only(args, w):
     ctx.close()
 
 
+def run_compare(args, w):
+    """The metric's comparison: Newton-PCG time per implicit step for each
+    basis and precision on identical inputs (same mesh, load ramp, steps).
+    One JSON line per (basis, precision), rank 0 only."""
+    import torch
+    import paper_2104_13466_gb300 as sd
+    mu, lam = lame(w["E"], w["nu"])
+    for prec_name in args.precisions.split(","):
+        prec = sd.MIXED_FP32 if prec_name == "mixed" else sd.FP64
+        for basis in args.bases.split(","):
+            ctx = sd.Context(w["elems"], w["lengths"], w["clamp"], mu, lam, w["rho"], w["P"], basis,
+                             precision=prec)
+            n = ctx.ndof
+            unit = torch.zeros(n, dtype=torch.float64, device="cuda")
+            ctx.traction_load(w["traction_face"], np.array(w["traction_dir"], dtype=float), unit)
+            smag = load_magnitude(w["load_key"])
+            u, v, a, Pn = (torch.zeros_like(unit) for _ in range(4))
+            opts = dict(newton_tol=w["newton_tol"], pcg_rtol=w["pcg_rtol"], mixed_rtol=args.mixed_rtol,
+                        pcg_maxit=args.pcg_maxit, max_newton=args.max_newton)
+            res = []
+            for k in range(1, args.warmup + args.steps + 1):
+                torch.mul(unit, smag * min(k, w["steps"]) / w["steps"], out=Pn)
+                ctx.set_timing(k > args.warmup)
+                t0 = ctx.timing()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                st = ctx.implicit_newmark_step(u, v, a, w["dt"], Pn, allow=(sd.NEWTON_DIVERGED, sd.PCG_MAXIT),
+                                               **opts)
+                e1.record()
+                torch.cuda.synchronize()
+                if k > args.warmup:
+                    t1 = ctx.timing()
+                    res.append({"step": k, "ms": e0.elapsed_time(e1), "newton_iters": st["newton_iters"],
+                                "pcg_iters": st["pcg_iters"], "converged": st["converged"],
+                                "residual_rel": st["residual_final"] / max(st["residual0"], 1e-300),
+                                "tangent_avg_ms": (t1["tangent_ms"] - t0["tangent_ms"]) /
+                                max(1, t1["tangent_launches"] - t0["tangent_launches"])})
+            tot_ms = sum(r["ms"] for r in res)
+            mv = sum(sum(r["pcg_iters"]) for r in res)
+            print(json.dumps({"mode": "compare", "workload": args.workload, "basis": basis, "precision": prec_name,
+                              "ms_per_step": tot_ms / len(res), "matvec_dofs_per_s": n * mv / (tot_ms * 1e-3),
+                              "pcg_iters_per_newton": mv / max(1, sum(r["newton_iters"] for r in res)),
+                              "steps": res}), flush=True)
+            ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -348,11 +395,16 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-only", action="store_true")
+    ap.add_argument("--compare", action="store_true")
+    ap.add_argument("--bases", default="nodal,modal,sdme_m,sdme_h")
+    ap.add_argument("--precisions", default="mixed,fp64")
     ap.add_argument("--kernel-iters", type=int, default=20)
     args = ap.parse_args()
     w = workload(args.workload)
     if args.kernel_only:
         run_kernel_only(args, w)
+    elif args.compare:
+        run_compare(args, w)
     elif args.impl == "reference":
         run_reference(args, w)
     else:

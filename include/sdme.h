@@ -216,6 +216,9 @@ typedef struct {
   int64_t kernel_launches; /* all kernels launched by this context */
 } sdme_timing;
 
+/* Description of the last CUDA runtime error the context met (after SDME_ECUDA). */
+const char* sdme_cuda_error_string(const sdme_ctx* ctx);
+
 /* Enable (1) / disable (0) CUDA-event timing of every tangent-kernel launch. */
 sdme_status sdme_set_timing(sdme_ctx* ctx, int enable);
 sdme_status sdme_get_timing(sdme_ctx* ctx, sdme_timing* out);

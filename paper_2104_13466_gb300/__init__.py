@@ -30,7 +30,7 @@ FACE_NAMES = {"xmin": XMIN, "xmax": XMAX, "ymin": YMIN, "ymax": YMAX, "zmin": ZM
 EXPORTS = ("sdme_status_string", "sdme_build_basis1d", "sdme_create", "sdme_destroy", "sdme_get_sizes",
            "sdme_internal_force", "sdme_mass_apply", "sdme_tangent_apply", "sdme_diagonal", "sdme_pcg_solve",
            "sdme_traction_load", "sdme_implicit_newmark_step", "sdme_set_timing", "sdme_get_timing",
-           "sdme_tangent_apply_noalloc")
+           "sdme_tangent_apply_noalloc", "sdme_cuda_error_string")
 
 
 class BasisDesc(ctypes.Structure):
@@ -78,6 +78,8 @@ def _load():
     vp, d, i, pd = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
     lib.sdme_status_string.restype = ctypes.c_char_p
     lib.sdme_status_string.argtypes = [i]
+    lib.sdme_cuda_error_string.restype = ctypes.c_char_p
+    lib.sdme_cuda_error_string.argtypes = [vp]
     lib.sdme_build_basis1d.argtypes = [ctypes.POINTER(BasisDesc), i, pd, pd, pd, pd, pd, pd]
     lib.sdme_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(MeshDesc), ctypes.POINTER(Material),
                                 ctypes.POINTER(BasisDesc), i, vp]
@@ -97,7 +99,7 @@ def _load():
     lib.sdme_tangent_apply_noalloc.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(Material), i, pd, pd, pd,
                                                pd, vp, d, vp, vp, vp]
     for name in EXPORTS:
-        if name != "sdme_status_string":
+        if name not in ("sdme_status_string", "sdme_cuda_error_string"):
             getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -106,14 +108,20 @@ lib = _load()
 
 
 class SdmeError(RuntimeError):
-    def __init__(self, status, where):
+    def __init__(self, status, where, detail=None):
         self.status = status
-        super().__init__("%s: %s (%d)" % (where, lib.sdme_status_string(status).decode(), status))
+        msg = "%s: %s (%d)" % (where, lib.sdme_status_string(status).decode(), status)
+        if detail:
+            msg += ": " + detail
+        super().__init__(msg)
 
 
-def _check(status, where, allow=()):
+def _check(status, where, allow=(), ctx=None):
     if status != OK and status not in allow:
-        raise SdmeError(status, where)
+        detail = None
+        if status == ECUDA and ctx is not None:
+            detail = lib.sdme_cuda_error_string(ctx).decode()
+        raise SdmeError(status, where, detail)
     return status
 
 
@@ -171,7 +179,7 @@ def tangent_apply_noalloc(elems, lengths, clamp, mu, lam, rho, P, tables, u, b1,
     stream = stream or torch.cuda.current_stream()
     return _check(lib.sdme_tangent_apply_noalloc(ctypes.byref(mesh), ctypes.byref(mat), int(P), *ptrs, _ptr(u),
                                                  float(b1), _ptr(x), _ptr(y), ctypes.c_void_p(stream.cuda_stream)),
-                  "sdme_tangent_apply_noalloc")
+                  "sdme_tangent_apply_noalloc", "sdme_cuda_error_string")
 
 
 class Context:
@@ -210,29 +218,29 @@ class Context:
             pass
 
     def internal_force(self, u, R):
-        return _check(lib.sdme_internal_force(self._h, _ptr(u), _ptr(R)), "sdme_internal_force")
+        return _check(lib.sdme_internal_force(self._h, _ptr(u), _ptr(R)), "sdme_internal_force", ctx=self._h)
 
     def mass_apply(self, x, y):
-        return _check(lib.sdme_mass_apply(self._h, _ptr(x), _ptr(y)), "sdme_mass_apply")
+        return _check(lib.sdme_mass_apply(self._h, _ptr(x), _ptr(y)), "sdme_mass_apply", ctx=self._h)
 
     def tangent_apply(self, u, b1, x, y):
-        return _check(lib.sdme_tangent_apply(self._h, _ptr(u), float(b1), _ptr(x), _ptr(y)), "sdme_tangent_apply")
+        return _check(lib.sdme_tangent_apply(self._h, _ptr(u), float(b1), _ptr(x), _ptr(y)), "sdme_tangent_apply", ctx=self._h)
 
     def diagonal(self, u, b1, d):
-        return _check(lib.sdme_diagonal(self._h, _ptr(u), float(b1), _ptr(d)), "sdme_diagonal")
+        return _check(lib.sdme_diagonal(self._h, _ptr(u), float(b1), _ptr(d)), "sdme_diagonal", ctx=self._h)
 
     def pcg_solve(self, u, b1, b, x, rtol=1e-10, maxit=20000, allow_maxit=False):
         its = ctypes.c_int()
         rel = ctypes.c_double()
         st = lib.sdme_pcg_solve(self._h, _ptr(u), float(b1), _ptr(b), _ptr(x), float(rtol), int(maxit),
                                 ctypes.byref(its), ctypes.byref(rel))
-        _check(st, "sdme_pcg_solve", allow=(PCG_MAXIT,) if allow_maxit else ())
+        _check(st, "sdme_pcg_solve", allow=(PCG_MAXIT,) if allow_maxit else (), ctx=self._h)
         return its.value, rel.value
 
     def traction_load(self, face, t, f):
         face = FACE_NAMES[face] if isinstance(face, str) else int(face)
         tt = (ctypes.c_double * 3)(*[float(v) for v in t])
-        return _check(lib.sdme_traction_load(self._h, face, tt, _ptr(f)), "sdme_traction_load")
+        return _check(lib.sdme_traction_load(self._h, face, tt, _ptr(f)), "sdme_traction_load", ctx=self._h)
 
     def implicit_newmark_step(self, u, v, a, dt, P_next, beta=0.25, gamma=0.5, newton_tol=1e-8, max_newton=30,
                               pcg_rtol=1e-10, mixed_rtol=1e-4, pcg_maxit=20000, allow=()):
@@ -243,7 +251,7 @@ class Context:
         stats = StepStats()
         status = lib.sdme_implicit_newmark_step(self._h, ctypes.byref(st), float(dt), _ptr(P_next),
                                                 ctypes.byref(opts), ctypes.byref(stats))
-        _check(status, "sdme_implicit_newmark_step", allow=allow)
+        _check(status, "sdme_implicit_newmark_step", allow=allow, ctx=self._h)
         n = min(stats.newton_iters, 32)
         return {"status": status, "newton_iters": stats.newton_iters, "pcg_iters_total": stats.pcg_iters_total,
                 "matvecs": stats.matvecs, "converged": bool(stats.converged), "residual0": stats.residual0,

@@ -20,7 +20,7 @@ using namespace sdme;
 namespace {
 
 constexpr int kVecBlocks = 152 * 4;      // per-DOF grid: 4 CTAs of 256 threads per SM
-constexpr int kPcgChunk = 8;             // iterations issued between host status reads
+constexpr int kPcgChunk = 16;            // iterations per CUDA graph / host status read
 
 #define SDME_CUDA(call)                                           \
   do {                                                            \
@@ -71,8 +71,17 @@ struct sdme_ctx {
   double* dscal_h = nullptr;
   int* err_h = nullptr;
 
+  // PCG runs on a private stream (graph capture is not possible on the
+  // legacy default stream), ordered after and before the caller's stream
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaGraphExec_t gexec[1] = {nullptr};   // one chunk of PCG iterations (untimed mode)
+  double gb1[1] = {0.0};
+
   // measurement
   bool timing = false;
+  int64_t timing_errors = 0;
+  cudaError_t last_timing_error = cudaSuccess;
   double tangent_ms = 0.0;
   int64_t tangent_launches = 0;
   int64_t kernel_launches = 0;
@@ -175,11 +184,47 @@ sdme_status norm2_host(sdme_ctx* ctx, const double* x, double* out) {
   return SDME_OK;
 }
 
+// Issue one chunk of PCG iterations (tangent, update, direction) on ctx->stream.
+template <typename T, typename TV>
+sdme_status pcg_chunk(sdme_ctx* ctx, double b1, bool tim, TV* r, TV* p, TV* q, TV* dinv, TV* xv) {
+  for (int j = 0; j < kPcgChunk; ++j) {
+    SDME_TRY((tangent_launch<T, TV>(ctx, b1, p, q, ctx->partial, ctx->scal, tim ? ctx->ev[2 * j] : nullptr,
+                                    tim ? ctx->ev[2 * j + 1] : nullptr)));
+    k_pcg_update<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, xv, r, p, q, dinv, ctx->scal,
+                                                                  ctx->partial);
+    k_pcg_direction<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, r, dinv, p, ctx->scal);
+  }
+  SDME_CUDA(cudaGetLastError());
+  return SDME_OK;
+}
+
+// Runs the PCG body on the context's private stream: the private stream
+// waits for the caller's stream on entry, and the caller's stream waits for
+// the private stream on exit (also on error paths).
+struct SideStreamScope {
+  sdme_ctx* ctx;
+  cudaStream_t user;
+  explicit SideStreamScope(sdme_ctx* c) : ctx(c), user(c->stream) {
+    cudaEventRecord(ctx->ev_fork, user);
+    cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+    ctx->stream = ctx->side;
+  }
+  ~SideStreamScope() {
+    cudaEventRecord(ctx->ev_join, ctx->side);
+    cudaStreamWaitEvent(user, ctx->ev_join, 0);
+    ctx->stream = user;
+  }
+};
+
 // Jacobi PCG on (b1 M + K_T) with the linearisation state already stored.
-// b and x are float64 device vectors; the iteration runs in TV / T.
+// b and x are float64 device vectors; the iteration runs in TV / T.  The
+// iterations are issued in chunks of kPcgChunk captured once as a CUDA graph
+// (kernels see the device-side status and return at once after convergence);
+// the host reads the status between chunks.
 template <typename T, typename TV>
 sdme_status pcg_core(sdme_ctx* ctx, double b1, const double* b, double* x, double rtol, int maxit, int* iters,
                      double* rel, TV* r, TV* p, TV* q, TV* dinv, TV* xv) {
+  SideStreamScope scope(ctx);
   SDME_TRY(diag_launch<T>(ctx, b1, (T*)dinv, 1));
   k_pcg_init<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, b, 1.0, dinv, xv, r, p, q, ctx->scal,
                                                               ctx->partial, rtol, maxit);
@@ -187,16 +232,35 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, const double* b, double* x, doubl
   ctx->kernel_launches += 1;
   int done_iters = 0;
   for (;;) {
+    // Per-launch event timing needs the events recorded by plain stream
+    // launches (events recorded inside a graph cannot be queried), so the
+    // timed mode issues the chunk directly; the untimed mode replays a graph.
     const bool tim = ctx->timing;
-    for (int j = 0; j < kPcgChunk; ++j) {
-      SDME_TRY((tangent_launch<T, TV>(ctx, b1, p, q, ctx->partial, ctx->scal, tim ? ctx->ev[2 * j] : nullptr,
-                                      tim ? ctx->ev[2 * j + 1] : nullptr)));
-      k_pcg_update<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, xv, r, p, q, dinv, ctx->scal,
-                                                                    ctx->partial);
-      k_pcg_direction<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, r, dinv, p, ctx->scal);
-      ctx->kernel_launches += 2;
+    cudaGraphExec_t& ge = ctx->gexec[0];
+    if (ge && ctx->gb1[0] != b1) {
+      cudaGraphExecDestroy(ge);
+      ge = nullptr;
     }
-    SDME_CUDA(cudaGetLastError());
+    if (tim) {
+      SDME_TRY((pcg_chunk<T, TV>(ctx, b1, true, r, p, q, dinv, xv)));
+    } else if (!ge) {
+      // first chunk runs directly (also sets the kernels' attributes), then
+      // the same chunk is captured for the following ones
+      SDME_TRY((pcg_chunk<T, TV>(ctx, b1, false, r, p, q, dinv, xv)));
+      cudaGraph_t g = nullptr;
+      SDME_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      sdme_status cs = pcg_chunk<T, TV>(ctx, b1, false, r, p, q, dinv, xv);
+      cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+      if (cs != SDME_OK) return cs;
+      SDME_CUDA(ce);
+      ce = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      SDME_CUDA(ce);
+      ctx->gb1[0] = b1;
+    } else {
+      SDME_CUDA(cudaGraphLaunch(ge, ctx->stream));
+    }
+    ctx->kernel_launches += 3 * kPcgChunk;
     SDME_CUDA(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(PcgScalars), cudaMemcpyDeviceToHost, ctx->stream));
     SDME_CUDA(cudaStreamSynchronize(ctx->stream));
     const PcgScalars& s = *ctx->scal_h;
@@ -207,9 +271,14 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, const double* b, double* x, doubl
       if (ran > kPcgChunk) ran = kPcgChunk;
       for (int j = 0; j < ran; ++j) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ctx->ev[2 * j], ctx->ev[2 * j + 1]) == cudaSuccess) {
+        const cudaError_t te = cudaEventElapsedTime(&ms, ctx->ev[2 * j], ctx->ev[2 * j + 1]);
+        if (te == cudaSuccess) {
           ctx->tangent_ms += ms;
           ctx->tangent_launches += 1;
+        } else {
+          ctx->timing_errors += 1;
+          ctx->last_timing_error = te;
+          cudaGetLastError();  // the failed query must not surface at the next launch check
         }
       }
     }
@@ -246,6 +315,11 @@ void free_all(sdme_ctx* ctx) {
   if (ctx->dscal_h) cudaFreeHost(ctx->dscal_h);
   if (ctx->err_h) cudaFreeHost(ctx->err_h);
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  for (cudaGraphExec_t g : ctx->gexec)
+    if (g) cudaGraphExecDestroy(g);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
 }
 
@@ -382,6 +456,9 @@ sdme_status sdme_create(sdme_ctx** out, const sdme_mesh_desc* mesh, const sdme_m
   if (ok) {
     ctx->ev.resize(2 * kPcgChunk);
     for (auto& e : ctx->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) == cudaSuccess;
   }
   if (ok) {
     ok = cudaMemsetAsync(ctx->err, 0, sizeof(int), ctx->stream) == cudaSuccess &&
@@ -555,6 +632,11 @@ sdme_status sdme_implicit_newmark_step(sdme_ctx* ctx, sdme_state* state, double 
   SDME_CUDA(cudaStreamSynchronize(s));
   if (stats) *stats = st;
   return result;
+}
+
+const char* sdme_cuda_error_string(const sdme_ctx* ctx) {
+  if (!ctx) return "no context";
+  return cudaGetErrorString(ctx->last_cuda != cudaSuccess ? ctx->last_cuda : ctx->last_timing_error);
 }
 
 sdme_status sdme_set_timing(sdme_ctx* ctx, int enable) {
