@@ -14,6 +14,8 @@ lambda = 100) scaled to the GPU problem sizes:
                 dead top traction ramped over 10 implicit Newmark steps.
 * ``beam_p8``   [0,8]x[0,1]x[0,1] cantilever, 64x8x8 hexes, P = 8, nu = 0.45;
                 x = 0 clamped, dead shear traction on x = 8 ramped over 20 steps.
+* ``beam_p8_dyn``  the same cantilever with dt = 3e-4, the paper's ratio of
+                time step to element wave-transit time (mass-dominated steps).
 * ``static_fab``  the paper's static fabricated problem (Sec. 5.1): unit cube,
                 2x2x2 hexes, x = 0 clamped.
 
@@ -38,6 +40,15 @@ WORKLOADS = {
         elems=(64, 8, 8), P=8, lengths=(8.0, 1.0, 1.0), E=1.0e3, nu=0.45, rho=1.0,
         clamp={"xmin": (0, 1, 2)}, traction_face="xmax", traction_dir=(0.0, 0.0, -1.0),
         steps=20, dt=1.0, newton_tol=1e-8, pcg_rtol=1e-10, k=0.5, lam=100.0,
+        load_key="beam_traction"),
+    # the same cantilever in the paper's dynamic regime: dt = 0.15 h / c_L
+    # (h = 0.125, c_L = sqrt((lambda + 2 mu) / rho) = 61.6 for nu = 0.45), the
+    # ratio of the paper's implicit fabricated tests (dt = 2e-3, h = 0.5,
+    # c_L = 36.7); the tip load is ramped over the same 20 steps
+    "beam_p8_dyn": dict(
+        elems=(64, 8, 8), P=8, lengths=(8.0, 1.0, 1.0), E=1.0e3, nu=0.45, rho=1.0,
+        clamp={"xmin": (0, 1, 2)}, traction_face="xmax", traction_dir=(0.0, 0.0, -1.0),
+        steps=20, dt=3.0e-4, newton_tol=1e-8, pcg_rtol=1e-10, k=0.5, lam=100.0,
         load_key="beam_traction"),
     "static_fab": dict(
         elems=(2, 2, 2), P=4, lengths=(1.0, 1.0, 1.0), E=1.0e3, nu=0.3, rho=1.0,
