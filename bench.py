@@ -56,6 +56,35 @@ def tangent_bytes(P, nelem, ndof, word_state, word_vec):
     return 10 * Q ** 3 * nelem * word_state + 3 * ndof * word_vec
 
 
+KERNEL_SOURCES = ("elem_kernels.cuh", "common.cuh", "elem_launch.cuh")
+
+
+def profiled_traffic(precision):
+    """DRAM bytes per tangent launch from the committed ncu summary, or None
+    when the kernel sources changed since that capture (hash mismatch)."""
+    import hashlib
+    name = "tangent_kernel_f32_beam_p8.md" if precision == "mixed" else "tangent_kernel_f64_beam_p8.md"
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2104_13466_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    vals = {}
+    for line in open(path):
+        line = line.strip()
+        for key in ("traffic_bytes_per_launch:", "kernel_source_sha256:"):
+            if line.startswith(key):
+                vals[key] = line.split(":", 1)[1].strip()
+    if vals.get("kernel_source_sha256:") != h.hexdigest():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch:"])
+    except (KeyError, ValueError):
+        return None
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -289,7 +318,9 @@ def run_gpu(args, w):
             "newton_pcg_ms_per_step": ms / args.steps,
             "steps_detail": [{k: s[k] for k in ("newton_iters", "pcg_iters_total", "converged")} for s in stats],
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": achieved_tf / alu_peak, "traffic": None,
+                         "frac": achieved_tf / alu_peak,
+                         "traffic": profiled_traffic(args.precision) if w["P"] == 8 and args.workload == "beam_p8"
+                         else None,
                          "kernel": "tangent_kernel<8,%s>" % ("float,float" if prec == sd.MIXED_FP32 else "double,double"),
                          "avg_launch_ms": avg_tan, "launches": tan_launches,
                          "flops_per_launch": flops, "peak_src": "derived from recipe unit counts and max clock",

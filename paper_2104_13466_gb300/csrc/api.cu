@@ -19,7 +19,7 @@ using namespace sdme;
 
 namespace {
 
-constexpr int kVecBlocks = 152 * 4;      // per-DOF grid: 4 CTAs of 256 threads per SM
+constexpr int kVecBlocks = 152 * 8;      // per-DOF grid: 8 CTAs of 256 threads per SM
 constexpr int kPcgChunk = 16;            // iterations per CUDA graph / host status read
 
 #define SDME_CUDA(call)                                           \

@@ -4,6 +4,8 @@
 // last CTA to arrive (deterministic order, no waiting).
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace sdme {
@@ -164,15 +166,57 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_init(MeshInfo mi, const dou
   }
 }
 
+// 16-byte vector of TV used by the streaming PCG kernels.
+template <typename TV>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int width = 4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int width = 2;
+};
+
+template <typename V>
+__device__ __forceinline__ auto& lane(V& v, int i) {
+  return reinterpret_cast<typename std::remove_reference<decltype(v.x)>::type*>(&v)[i];
+}
+
 template <typename TV>
 __global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TV* __restrict__ x, TV* __restrict__ r,
                                                             const TV* __restrict__ p, TV* __restrict__ q,
                                                             const TV* __restrict__ dinv, PcgScalars* scal,
                                                             double* __restrict__ partial) {
   if (scal->status != kPcgRunning) return;
+  using V = typename Vec16<TV>::type;
+  constexpr int W = Vec16<TV>::width;
   const TV alpha = (TV)scal->alpha;
   TV srz = TV(0), srr = TV(0);
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t nv = n / W;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t g = t0; g < nv; g += stride) {
+    V xv = reinterpret_cast<const V*>(x)[g];
+    V rv = reinterpret_cast<const V*>(r)[g];
+    V pv = reinterpret_cast<const V*>(p)[g];
+    V qv = reinterpret_cast<const V*>(q)[g];
+    V dv = reinterpret_cast<const V*>(dinv)[g];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      lane(xv, i) += alpha * lane(pv, i);
+      const TV ri = lane(rv, i) - alpha * lane(qv, i);
+      lane(rv, i) = ri;
+      srz += ri * (lane(dv, i) * ri);
+      srr += ri * ri;
+    }
+    reinterpret_cast<V*>(x)[g] = xv;
+    reinterpret_cast<V*>(r)[g] = rv;
+    reinterpret_cast<V*>(q)[g] = V{};
+  }
+  for (int64_t g = nv * W + t0; g < n; g += stride) {  // tail
     const TV qv = q[g];
     x[g] += alpha * p[g];
     const TV rv = r[g] - alpha * qv;
@@ -212,9 +256,21 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_direction(int64_t n, const 
                                                                const TV* __restrict__ dinv, TV* __restrict__ p,
                                                                const PcgScalars* scal) {
   if (scal->status != kPcgRunning) return;
+  using V = typename Vec16<TV>::type;
+  constexpr int W = Vec16<TV>::width;
   const TV beta = (TV)scal->beta;
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
-    p[g] = dinv[g] * r[g] + beta * p[g];
+  const int64_t nv = n / W;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t g = t0; g < nv; g += stride) {
+    V rv = reinterpret_cast<const V*>(r)[g];
+    V dv = reinterpret_cast<const V*>(dinv)[g];
+    V pv = reinterpret_cast<const V*>(p)[g];
+#pragma unroll
+    for (int i = 0; i < W; ++i) lane(pv, i) = lane(dv, i) * lane(rv, i) + beta * lane(pv, i);
+    reinterpret_cast<V*>(p)[g] = pv;
+  }
+  for (int64_t g = nv * W + t0; g < n; g += stride) p[g] = dinv[g] * r[g] + beta * p[g];
 }
 
 // out = scale * x (TV -> float64)
