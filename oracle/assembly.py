@@ -97,6 +97,18 @@ class Discretization:
             out += self.scatter(De, s)
         return np.where(self.mask, 1.0, out)
 
+    def mass_diagonal(self):
+        """diag(M): rho sum_q w_q N_m(q)^2 summed over elements."""
+        De = self.rho * (self.ref.w @ (self.ref.N * self.ref.N))
+        out = np.zeros(self.mesh.ndof)
+        for s in self._chunks():
+            E = s.stop - s.start
+            out += self.scatter(np.broadcast_to(De, (E, 3, De.size)).copy(), s)
+        return out
+
+    def kinetic_energy(self, v):
+        return 0.5 * float(v @ self.mass_apply(v))
+
     def tangent_matrix(self, u, b1=0.0, masked=True):
         """Global sparse b1 M + K_T(u) (tiny meshes)."""
         ref = self.ref

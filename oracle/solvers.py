@@ -122,3 +122,41 @@ def initial_acceleration(disc, u0, P0):
     rhs = P0 - disc.internal_force(u0)
     rhs[disc.mask] = 0.0
     return spla.spsolve(Mm.tocsc(), rhs)
+
+
+def _masked_mass(disc):
+    """Consistent mass with constrained rows/columns replaced by identity."""
+    import scipy.sparse as sp
+    M = disc.mass_matrix()
+    keep = sp.diags((~disc.mask).astype(float))
+    return (keep @ M @ keep + sp.diags(disc.mask.astype(float))).tocsc()
+
+
+def mass_solve(disc, rhs, linear="direct", rtol=1e-13, Mm=None):
+    """a = M^{-1} rhs on free DOFs (constrained entries 0)."""
+    rhs = np.where(disc.mask, 0.0, rhs)
+    if linear == "direct":
+        import scipy.sparse.linalg as spla
+        return spla.spsolve(Mm if Mm is not None else _masked_mass(disc), rhs)
+    d = np.where(disc.mask, 1.0, disc.mass_diagonal())
+    a, _, _ = jacobi_pcg(lambda x: np.where(disc.mask, x, disc.mass_apply(np.where(disc.mask, 0.0, x))), rhs, d,
+                         rtol)
+    return a
+
+
+def central_difference_start(disc, u0, v0, P0, dt, linear="direct"):
+    """Start-up of the central-difference scheme (Sec. 4.1):
+    a_0 = M^{-1} (P_0 - R(u_0)),  u_{-1} = u_0 - dt v_0 + dt^2 / 2 a_0."""
+    a0 = mass_solve(disc, P0 - disc.internal_force(u0), linear)
+    return u0 - dt * v0 + 0.5 * dt * dt * a0, a0
+
+
+def central_difference_step(disc, u, u_prev, Pn, dt, linear="direct", Mm=None):
+    """One explicit step (Sec. 4.1, eq. Motion_explicit2):
+    (M / dt^2) u_{n+1} = P_n - R(u_n) + (M / dt^2)(2 u_n - u_{n-1}),
+    solved as M a_n = P_n - R(u_n), u_{n+1} = 2 u_n - u_{n-1} + dt^2 a_n.
+    Constrained DOFs keep their values.  Returns (u_{n+1}, a_n)."""
+    a = mass_solve(disc, Pn - disc.internal_force(u), linear, Mm=Mm)
+    unew = 2.0 * u - u_prev + dt * dt * a
+    unew[disc.mask] = u[disc.mask]
+    return unew, a
