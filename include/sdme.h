@@ -209,6 +209,50 @@ sdme_status sdme_implicit_newmark_step(sdme_ctx* ctx, sdme_state* state, double 
                                        const double* P_next_dev, const sdme_newton_opts* opts,
                                        sdme_step_stats* stats);
 
+/* State of the explicit central-difference scheme (device vectors, ndof each). */
+typedef struct {
+  double* u;             /* u_n (in) -> u_{n+1} (out); the call swaps u and u_prev */
+  double* u_prev;        /* u_{n-1} (in) -> u_n (out) */
+  double* a;             /* a_n = M^{-1} (P_n - R(u_n)) (out) */
+} sdme_explicit_state;
+
+/*
+ * Start-up of the explicit central-difference scheme (Sec. 4.1):
+ * a_0 = M^{-1} (P_0 - R(u_0)) by Jacobi-PCG on the consistent mass (rtol,
+ * maxit), and u_{-1} = u_0 - dt v_0 + dt^2/2 a_0 written to state->u_prev
+ * (constrained DOFs: u_{-1} = u_0).  state->u holds u_0 on entry.
+ */
+sdme_status sdme_explicit_start(sdme_ctx* ctx, sdme_explicit_state* state, double dt, const double* P0_dev,
+                                const double* v0_dev, double rtol, int maxit);
+
+/*
+ * One explicit central-difference step (Sec. 4.1, eq. Motion_explicit2):
+ * M a_n = P_n - R(u_n) solved by Jacobi-PCG on the consistent mass (rtol
+ * relative, from zero), u_{n+1} = 2 u_n - u_{n-1} + dt^2 a_n on free DOFs.
+ * The new displacement is written over u_{n-1} and the two pointers in
+ * `state` are swapped, so state->u is u_{n+1} on return.  The mass solve
+ * runs in the context's precision (float32 vectors for SDME_MIXED_FP32);
+ * the residual and the state update are float64.  pcg_iters may be NULL.
+ */
+sdme_status sdme_explicit_step(sdme_ctx* ctx, sdme_explicit_state* state, double dt, const double* Pn_dev,
+                               double rtol, int maxit, int* pcg_iters);
+
+/*
+ * Kinetic energy 1/2 v^T M v and strain energy int Psi(F(u)) dV (eq.
+ * hyperelastic strain energy); either output may be NULL (its input may
+ * then be NULL too).  Float64, synchronises.
+ */
+sdme_status sdme_energy(sdme_ctx* ctx, const double* u_dev, const double* v_dev, double* kinetic, double* strain);
+
+/*
+ * Critical explicit time step of the linearisation at u: power iteration on
+ * M^{-1} K_T(u) (iters iterations, Rayleigh quotient, constrained DOFs
+ * excluded) gives lambda_max; dt_crit = 2 / sqrt(lambda_max) (the central-
+ * difference stability limit).  Either output may be NULL.
+ */
+sdme_status sdme_estimate_dt_crit(sdme_ctx* ctx, const double* u_dev, int iters, double* dt_crit,
+                                  double* lambda_max);
+
 /* Cumulative device event timings of the context (ms) and counts, for measurement. */
 typedef struct {
   double tangent_ms;     /* sum of timed tangent-kernel launches */

@@ -30,7 +30,8 @@ FACE_NAMES = {"xmin": XMIN, "xmax": XMAX, "ymin": YMIN, "ymax": YMAX, "zmin": ZM
 EXPORTS = ("sdme_status_string", "sdme_build_basis1d", "sdme_create", "sdme_destroy", "sdme_get_sizes",
            "sdme_internal_force", "sdme_mass_apply", "sdme_tangent_apply", "sdme_diagonal", "sdme_pcg_solve",
            "sdme_traction_load", "sdme_implicit_newmark_step", "sdme_set_timing", "sdme_get_timing",
-           "sdme_tangent_apply_noalloc", "sdme_cuda_error_string")
+           "sdme_tangent_apply_noalloc", "sdme_cuda_error_string", "sdme_explicit_start", "sdme_explicit_step",
+           "sdme_energy", "sdme_estimate_dt_crit")
 
 
 class BasisDesc(ctypes.Structure):
@@ -60,6 +61,10 @@ class StepStats(ctypes.Structure):
 
 class State(ctypes.Structure):
     _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("a", ctypes.c_void_p)]
+
+
+class ExplicitState(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("u_prev", ctypes.c_void_p), ("a", ctypes.c_void_p)]
 
 
 class Timing(ctypes.Structure):
@@ -94,6 +99,10 @@ def _load():
     lib.sdme_traction_load.argtypes = [vp, i, pd, vp]
     lib.sdme_implicit_newmark_step.argtypes = [vp, ctypes.POINTER(State), d, vp, ctypes.POINTER(NewtonOpts),
                                                ctypes.POINTER(StepStats)]
+    lib.sdme_explicit_start.argtypes = [vp, ctypes.POINTER(ExplicitState), d, vp, vp, d, i]
+    lib.sdme_explicit_step.argtypes = [vp, ctypes.POINTER(ExplicitState), d, vp, d, i, ctypes.POINTER(i)]
+    lib.sdme_energy.argtypes = [vp, vp, vp, pd, pd]
+    lib.sdme_estimate_dt_crit.argtypes = [vp, vp, i, pd, pd]
     lib.sdme_set_timing.argtypes = [vp, i]
     lib.sdme_get_timing.argtypes = [vp, ctypes.POINTER(Timing)]
     lib.sdme_tangent_apply_noalloc.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(Material), i, pd, pd, pd,
@@ -179,7 +188,23 @@ def tangent_apply_noalloc(elems, lengths, clamp, mu, lam, rho, P, tables, u, b1,
     stream = stream or torch.cuda.current_stream()
     return _check(lib.sdme_tangent_apply_noalloc(ctypes.byref(mesh), ctypes.byref(mat), int(P), *ptrs, _ptr(u),
                                                  float(b1), _ptr(x), _ptr(y), ctypes.c_void_p(stream.cuda_stream)),
-                  "sdme_tangent_apply_noalloc", "sdme_cuda_error_string")
+                  "sdme_tangent_apply_noalloc", "sdme_cuda_error_string", "sdme_explicit_start", "sdme_explicit_step",
+           "sdme_energy", "sdme_estimate_dt_crit")
+
+
+class _ExplicitStateHolder:
+    """Keeps the tensors of an sdme_explicit_state alive and tracks which
+    tensor currently holds u_n and u_{n-1} after the library swaps them."""
+
+    def __init__(self, u, u_prev, a):
+        self._t = {u.data_ptr(): u, u_prev.data_ptr(): u_prev}
+        self.a = a
+        self.c = ExplicitState(u.data_ptr(), u_prev.data_ptr(), a.data_ptr())
+        self.sync()
+
+    def sync(self):
+        self.u = self._t[self.c.u]
+        self.u_prev = self._t[self.c.u_prev]
 
 
 class Context:
@@ -257,6 +282,41 @@ class Context:
                 "matvecs": stats.matvecs, "converged": bool(stats.converged), "residual0": stats.residual0,
                 "residual_final": stats.residual_final, "pcg_iters": list(stats.pcg_iters[:n]),
                 "residuals": list(stats.residuals[:n + 1])}
+
+    # -- explicit central difference (Sec. 4.1) ------------------------------
+    def explicit_state(self, u, u_prev, a):
+        """Bundle three float64 CUDA tensors (u_n, u_{n-1}, a_n) for the
+        explicit calls; the calls swap which tensor holds u and u_prev, read
+        the current assignment from ``current()``."""
+        for t in (u, u_prev, a):
+            _ptr(t)
+        return _ExplicitStateHolder(u, u_prev, a)
+
+    def explicit_start(self, st, dt, P0, v0, rtol=1e-12, maxit=20000):
+        return _check(lib.sdme_explicit_start(self._h, ctypes.byref(st.c), float(dt), _ptr(P0), _ptr(v0),
+                                              float(rtol), int(maxit)), "sdme_explicit_start", ctx=self._h)
+
+    def explicit_step(self, st, dt, Pn, rtol=1e-12, maxit=20000):
+        its = ctypes.c_int()
+        _check(lib.sdme_explicit_step(self._h, ctypes.byref(st.c), float(dt), _ptr(Pn), float(rtol), int(maxit),
+                                      ctypes.byref(its)), "sdme_explicit_step", ctx=self._h)
+        st.sync()
+        return its.value
+
+    def energy(self, u=None, v=None):
+        ke = ctypes.c_double()
+        se = ctypes.c_double()
+        _check(lib.sdme_energy(self._h, _ptr(u) if u is not None else None, _ptr(v) if v is not None else None,
+                               ctypes.byref(ke) if v is not None else None,
+                               ctypes.byref(se) if u is not None else None), "sdme_energy", ctx=self._h)
+        return (ke.value if v is not None else None), (se.value if u is not None else None)
+
+    def estimate_dt_crit(self, u, iters=50):
+        dt = ctypes.c_double()
+        lam = ctypes.c_double()
+        _check(lib.sdme_estimate_dt_crit(self._h, _ptr(u), int(iters), ctypes.byref(dt), ctypes.byref(lam)),
+               "sdme_estimate_dt_crit", ctx=self._h)
+        return dt.value, lam.value
 
     def set_timing(self, enable=True):
         return _check(lib.sdme_set_timing(self._h, int(bool(enable))), "sdme_set_timing")

@@ -77,6 +77,8 @@ struct sdme_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t gexec[1] = {nullptr};   // one chunk of PCG iterations (untimed mode)
   double gb1[1] = {0.0};
+  bool gmass = false;
+  int gsize = 0;
 
   // measurement
   bool timing = false;
@@ -120,12 +122,13 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
 }
 
-sdme_status residual_launch(sdme_ctx* ctx, double b1, const double* u, double* y) {
+sdme_status residual_launch(sdme_ctx* ctx, double b1, const double* u, double* y, bool with_state = true) {
   const HostElemData& h = ctx->h;
-  float* st32 = (ctx->prec == SDME_MIXED_FP32) ? ctx->st32 : nullptr;
+  float* st32 = (with_state && ctx->prec == SDME_MIXED_FP32) ? ctx->st32 : nullptr;
+  double* st64 = with_state ? ctx->st64 : nullptr;
   SDME_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * ctx->ndof, ctx->stream));
   SDME_CUDA(dispatch_P(h.P, [&](auto Pc) {
-    return launch_residual<decltype(Pc)::value>(h, b1, u, y, ctx->st64, st32, ctx->err, ctx->stream);
+    return launch_residual<decltype(Pc)::value>(h, b1, u, y, st64, st32, ctx->err, ctx->stream);
   }));
   ctx->kernel_launches += 1;
   return SDME_OK;
@@ -186,10 +189,17 @@ sdme_status norm2_host(sdme_ctx* ctx, const double* x, double* out) {
 
 // Issue one chunk of PCG iterations (tangent, update, direction) on ctx->stream.
 template <typename T, typename TV>
-sdme_status pcg_chunk(sdme_ctx* ctx, double b1, bool tim, TV* r, TV* p, TV* q, TV* dinv, TV* xv) {
+sdme_status pcg_chunk(sdme_ctx* ctx, double b1, bool mass_only, bool tim, TV* r, TV* p, TV* q, TV* dinv, TV* xv) {
   for (int j = 0; j < kPcgChunk; ++j) {
-    SDME_TRY((tangent_launch<T, TV>(ctx, b1, p, q, ctx->partial, ctx->scal, tim ? ctx->ev[2 * j] : nullptr,
-                                    tim ? ctx->ev[2 * j + 1] : nullptr)));
+    if (mass_only) {
+      SDME_CUDA(dispatch_P(ctx->h.P, [&](auto Pc) {
+        return launch_mass_op<decltype(Pc)::value, T, TV>(ctx->h, b1, p, q, ctx->partial, ctx->scal, ctx->stream);
+      }));
+      ctx->kernel_launches += 1;
+    } else {
+      SDME_TRY((tangent_launch<T, TV>(ctx, b1, p, q, ctx->partial, ctx->scal, tim ? ctx->ev[2 * j] : nullptr,
+                                      tim ? ctx->ev[2 * j + 1] : nullptr)));
+    }
     k_pcg_update<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, xv, r, p, q, dinv, ctx->scal,
                                                                   ctx->partial);
     k_pcg_direction<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, r, dinv, p, ctx->scal);
@@ -222,10 +232,20 @@ struct SideStreamScope {
 // (kernels see the device-side status and return at once after convergence);
 // the host reads the status between chunks.
 template <typename T, typename TV>
-sdme_status pcg_core(sdme_ctx* ctx, double b1, const double* b, double* x, double rtol, int maxit, int* iters,
-                     double* rel, TV* r, TV* p, TV* q, TV* dinv, TV* xv) {
+sdme_status pcg_core(sdme_ctx* ctx, double b1, bool mass_only, const double* b, double* x, double rtol, int maxit,
+                     int* iters, double* rel, TV* r, TV* p, TV* q, TV* dinv, TV* xv) {
   SideStreamScope scope(ctx);
-  SDME_TRY(diag_launch<T>(ctx, b1, (T*)dinv, 1));
+  if (mass_only) {
+    SDME_CUDA(cudaMemsetAsync(dinv, 0, sizeof(TV) * ctx->ndof, ctx->stream));
+    SDME_CUDA(dispatch_P(ctx->h.P, [&](auto Pc) {
+      return launch_mass_diag<decltype(Pc)::value, T>(ctx->h, b1, (T*)dinv, ctx->stream);
+    }));
+    k_diag_finish<T><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, (T*)dinv, 1);
+    SDME_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 2;
+  } else {
+    SDME_TRY(diag_launch<T>(ctx, b1, (T*)dinv, 1));
+  }
   k_pcg_init<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, b, 1.0, dinv, xv, r, p, q, ctx->scal,
                                                               ctx->partial, rtol, maxit);
   SDME_CUDA(cudaGetLastError());
@@ -237,19 +257,19 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, const double* b, double* x, doubl
     // timed mode issues the chunk directly; the untimed mode replays a graph.
     const bool tim = ctx->timing;
     cudaGraphExec_t& ge = ctx->gexec[0];
-    if (ge && ctx->gb1[0] != b1) {
+    if (ge && (ctx->gb1[0] != b1 || ctx->gmass != mass_only || ctx->gsize != (int)sizeof(T))) {
       cudaGraphExecDestroy(ge);
       ge = nullptr;
     }
     if (tim) {
-      SDME_TRY((pcg_chunk<T, TV>(ctx, b1, true, r, p, q, dinv, xv)));
+      SDME_TRY((pcg_chunk<T, TV>(ctx, b1, mass_only, true, r, p, q, dinv, xv)));
     } else if (!ge) {
       // first chunk runs directly (also sets the kernels' attributes), then
       // the same chunk is captured for the following ones
-      SDME_TRY((pcg_chunk<T, TV>(ctx, b1, false, r, p, q, dinv, xv)));
+      SDME_TRY((pcg_chunk<T, TV>(ctx, b1, mass_only, false, r, p, q, dinv, xv)));
       cudaGraph_t g = nullptr;
       SDME_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-      sdme_status cs = pcg_chunk<T, TV>(ctx, b1, false, r, p, q, dinv, xv);
+      sdme_status cs = pcg_chunk<T, TV>(ctx, b1, mass_only, false, r, p, q, dinv, xv);
       cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
       if (cs != SDME_OK) return cs;
       SDME_CUDA(ce);
@@ -257,6 +277,8 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, const double* b, double* x, doubl
       cudaGraphDestroy(g);
       SDME_CUDA(ce);
       ctx->gb1[0] = b1;
+      ctx->gmass = mass_only;
+      ctx->gsize = (int)sizeof(T);
     } else {
       SDME_CUDA(cudaGraphLaunch(ge, ctx->stream));
     }
@@ -297,12 +319,23 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, const double* b, double* x, doubl
 }
 
 sdme_status pcg_dispatch(sdme_ctx* ctx, double b1, const double* b, double* x, double rtol, int maxit,
-                         int* iters, double* rel) {
+                         int* iters, double* rel, bool mass_only = false) {
   if (ctx->prec == SDME_MIXED_FP32)
-    return pcg_core<float, float>(ctx, b1, b, x, rtol, maxit, iters, rel, ctx->r32, ctx->p32, ctx->q32, ctx->d32,
-                                  ctx->x32);
-  return pcg_core<double, double>(ctx, b1, b, x, rtol, maxit, iters, rel, ctx->r64, ctx->p64, ctx->q64, ctx->d64,
-                                  ctx->x64);
+    return pcg_core<float, float>(ctx, b1, mass_only, b, x, rtol, maxit, iters, rel, ctx->r32, ctx->p32, ctx->q32,
+                                  ctx->d32, ctx->x32);
+  return pcg_core<double, double>(ctx, b1, mass_only, b, x, rtol, maxit, iters, rel, ctx->r64, ctx->p64, ctx->q64,
+                                  ctx->d64, ctx->x64);
+}
+
+// x . y (float64, deterministic), synchronises
+sdme_status dot_host(sdme_ctx* ctx, const double* x, const double* y, double* out) {
+  k_dot<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, x, y, ctx->partial, ctx->dcount, ctx->dscal);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 1;
+  SDME_CUDA(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  SDME_CUDA(cudaStreamSynchronize(ctx->stream));
+  *out = ctx->dscal_h[0];
+  return SDME_OK;
 }
 
 void free_all(sdme_ctx* ctx) {
@@ -632,6 +665,111 @@ sdme_status sdme_implicit_newmark_step(sdme_ctx* ctx, sdme_state* state, double 
   SDME_CUDA(cudaStreamSynchronize(s));
   if (stats) *stats = st;
   return result;
+}
+
+sdme_status sdme_explicit_start(sdme_ctx* ctx, sdme_explicit_state* st, double dt, const double* P0_dev,
+                                const double* v0_dev, double rtol, int maxit) {
+  if (!ctx || !st || !st->u || !st->u_prev || !st->a || !P0_dev || !v0_dev || !(dt > 0.0) || maxit < 1)
+    return SDME_EINVAL;
+  SDME_TRY(residual_launch(ctx, 0.0, st->u, ctx->y, false));
+  k_residual_combine<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, P0_dev, nullptr, ctx->y, ctx->psi,
+                                                                  ctx->partial, ctx->dcount, ctx->dscal);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 1;
+  SDME_TRY(sync_and_check(ctx));
+  int its = 0;
+  double rel = 0.0;
+  sdme_status ps = pcg_dispatch(ctx, 1.0, ctx->psi, st->a, rtol, maxit, &its, &rel, true);
+  if (ps != SDME_OK) return ps;
+  k_cd_start<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, st->u, v0_dev, st->a, dt, st->u_prev);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 1;
+  SDME_CUDA(cudaStreamSynchronize(ctx->stream));
+  return SDME_OK;
+}
+
+sdme_status sdme_explicit_step(sdme_ctx* ctx, sdme_explicit_state* st, double dt, const double* Pn_dev, double rtol,
+                               int maxit, int* pcg_iters) {
+  if (!ctx || !st || !st->u || !st->u_prev || !st->a || !Pn_dev || !(dt > 0.0) || maxit < 1) return SDME_EINVAL;
+  SDME_TRY(residual_launch(ctx, 0.0, st->u, ctx->y, false));
+  k_residual_combine<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, Pn_dev, nullptr, ctx->y, ctx->psi,
+                                                                  ctx->partial, ctx->dcount, ctx->dscal);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 1;
+  int its = 0;
+  double rel = 0.0;
+  sdme_status ps = pcg_dispatch(ctx, 1.0, ctx->psi, st->a, rtol, maxit, &its, &rel, true);
+  if (pcg_iters) *pcg_iters = its;
+  if (ps != SDME_OK) return ps;
+  // u_{n+1} = 2 u_n - u_{n-1} + dt^2 a_n, written over u_{n-1}; then swap
+  k_cd_update<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, st->u, st->a, dt * dt, st->u_prev);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 1;
+  double* t = st->u;
+  st->u = st->u_prev;
+  st->u_prev = t;
+  return sync_and_check(ctx);
+}
+
+sdme_status sdme_energy(sdme_ctx* ctx, const double* u_dev, const double* v_dev, double* kinetic, double* strain) {
+  if (!ctx) return SDME_EINVAL;
+  if (kinetic) {
+    if (!v_dev) return SDME_EINVAL;
+    SDME_TRY(sdme_mass_apply(ctx, v_dev, ctx->y));
+    double vmv = 0.0;
+    SDME_TRY(dot_host(ctx, v_dev, ctx->y, &vmv));
+    *kinetic = 0.5 * vmv;
+  }
+  if (strain) {
+    if (!u_dev) return SDME_EINVAL;
+    SDME_CUDA(dispatch_P(ctx->h.P, [&](auto Pc) {
+      return launch_energy<decltype(Pc)::value>(ctx->h, u_dev, ctx->partial, ctx->dcount, ctx->dscal, ctx->err,
+                                                ctx->stream);
+    }));
+    ctx->kernel_launches += 1;
+    SDME_CUDA(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    SDME_TRY(sync_and_check(ctx));
+    *strain = ctx->dscal_h[0];
+  }
+  return SDME_OK;
+}
+
+sdme_status sdme_estimate_dt_crit(sdme_ctx* ctx, const double* u_dev, int iters, double* dt_crit,
+                                  double* lambda_max) {
+  if (!ctx || !u_dev || iters < 1) return SDME_EINVAL;
+  // linearise at u, then power iteration x <- M^{-1} K_T x / |.| with the
+  // Rayleigh quotient x.Kx / x.Mx; constrained DOFs stay zero
+  SDME_TRY(residual_launch(ctx, 0.0, u_dev, ctx->y));
+  SDME_TRY(sync_and_check(ctx));
+  double* x = ctx->du;
+  double* Kx = ctx->ahat;
+  double* Mx = ctx->mhat;
+  k_fill_hash<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, x, 12345u);
+  SDME_CUDA(cudaGetLastError());
+  double lam = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    double xx = 0.0;
+    SDME_TRY(dot_host(ctx, x, x, &xx));
+    if (!(xx > 0.0)) return SDME_NAN;
+    k_scale<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, 1.0 / std::sqrt(xx), x);
+    k_mask_init<double><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, x, Kx);
+    SDME_CUDA(cudaGetLastError());
+    SDME_TRY((tangent_launch<double, double>(ctx, 0.0, x, Kx, nullptr, nullptr)));
+    SDME_TRY(sdme_mass_apply(ctx, x, Mx));
+    double xKx = 0.0, xMx = 0.0;
+    SDME_TRY(dot_host(ctx, x, Kx, &xKx));
+    SDME_TRY(dot_host(ctx, x, Mx, &xMx));
+    lam = xKx / xMx;
+    int its = 0;
+    double rel = 0.0;
+    sdme_status ps = pcg_dispatch(ctx, 1.0, Kx, x, 1e-6, 2000, &its, &rel, true);
+    if (ps != SDME_OK && ps != SDME_PCG_MAXIT) return ps;
+    ctx->kernel_launches += 3;
+  }
+  if (!(lam > 0.0)) return SDME_NAN;
+  if (lambda_max) *lambda_max = lam;
+  if (dt_crit) *dt_crit = 2.0 / std::sqrt(lam);
+  return SDME_OK;
 }
 
 const char* sdme_cuda_error_string(const sdme_ctx* ctx) {

@@ -406,7 +406,9 @@ constexpr int tangent_min_blocks() {
   return sizeof(T) == 4 ? 4 : 2;
 }
 
-template <int P, typename T, typename TV>
+// STIFF = false gives the mass-only operator y += b1 M x (same masking and
+// PCG coupling, no linearisation state): the explicit scheme's system matrix.
+template <int P, typename T, typename TV, bool STIFF = true>
 __global__ void __launch_bounds__(elem_threads(P), tangent_min_blocks<T>())
 tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restrict__ x,
                TV* __restrict__ y, const T* __restrict__ st, double* __restrict__ dot_partial,
@@ -426,10 +428,19 @@ tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restric
     X[so] = cons ? T(0) : (T)x[g];
   }
   __syncthreads();
-  forward_stages<T, P, true>(prm.tab, sm);
+  forward_stages<T, P, STIFF>(prm.tab, sm);
   const T sc[3] = {prm.s[0], prm.s[1], prm.s[2]};
   const T* ste = st + (int64_t)e * kStateFields * Q3;
-  for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
+  if constexpr (!STIFF) {
+    for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
+      const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
+      const int so = (qz * Q + qy) * XQ + qx;
+      const T mfac = prm.b1 * prm.rho * prm.tab.W[qx] * prm.tab.W[qy] * prm.tab.W[qz] * prm.detJ;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= mfac;
+    }
+  }
+  for (int q = threadIdx.x; STIFF && q < Q3; q += blockDim.x) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
     const int so = (qz * Q + qy) * XQ + qx;
     T H[3][3], dF[3][3];
@@ -467,7 +478,7 @@ tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restric
     for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= mfac;
   }
   __syncthreads();
-  transpose_stages<T, P, true>(prm.tab, sm);
+  transpose_stages<T, P, STIFF>(prm.tab, sm);
   T dotT = T(0);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
@@ -636,6 +647,93 @@ diag_kernel(const __grid_constant__ ElemParams<T, P> prm, const T* __restrict__ 
       bool cons;
       int64_t g = dof_index(prm, P, ex, ey, ez, c * n3 + m, &cons);
       if (!cons) atomicAdd(&y[g], acc);
+    }
+  }
+}
+
+//-----------------------------------------------------------------------------
+// Mass diagonal: y += b1 diag(M) on free DOFs.  On an axis-aligned box the
+// element mass diagonal factors as b1 rho detJ m_p m_q m_r with
+// m_j = sum_k W_k B_kj^2.
+//-----------------------------------------------------------------------------
+template <int P, typename T>
+__global__ void __launch_bounds__(256) mass_diag_kernel(const __grid_constant__ ElemParams<T, P> prm,
+                                                        T* __restrict__ y) {
+  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n;
+  __shared__ T m1[n];
+  if (threadIdx.x < n) {
+    T acc = T(0);
+    for (int k = 0; k < Q; ++k) acc += prm.tab.W[k] * prm.tab.B[k * n + threadIdx.x] * prm.tab.B[k * n + threadIdx.x];
+    m1[threadIdx.x] = acc;
+  }
+  __syncthreads();
+  const int e = blockIdx.x;
+  const ElemView<ElemParams<T, P>> view(prm, P, e);
+  const T f = prm.b1 * prm.rho * prm.detJ;
+  for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
+    bool cons;
+    int so;
+    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
+    const int m = idx % n3, p = m % n, q = (m / n) % n, r = m / (n * n);
+    if (!cons) atomicAdd(&y[g], f * m1[p] * m1[q] * m1[r]);
+  }
+}
+
+//-----------------------------------------------------------------------------
+// Strain energy: partial[e] = int_e Psi(F) dV with the neo-Hookean energy of
+// eq. hyperelastic strain energy, Psi = mu/2 (tr C - 3) - mu ln J + lambda/2 (ln J)^2;
+// the last CTA writes the sum (fixed order) to *out.
+//-----------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(elem_threads(P))
+energy_kernel(const __grid_constant__ ElemParams<double, P> prm, const double* __restrict__ u,
+              double* __restrict__ partial, unsigned int* counter, double* out, int* __restrict__ err) {
+  using T = double;
+  using G = Geo<P>;
+  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* X = sm + 3 * FQ;
+  const int e = blockIdx.x;
+  const ElemView<ElemParams<double, P>> view(prm, P, e);
+  for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
+    bool cons;
+    int so;
+    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
+    X[so] = u[g];
+  }
+  __syncthreads();
+  forward_stages<T, P, true>(prm.tab, sm);
+  const T sc[3] = {prm.s[0], prm.s[1], prm.s[2]};
+  T acc = T(0);
+  for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
+    const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
+    const int so = (qz * Q + qy) * XQ + qx;
+    T F[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) F[c][d] = (c == d ? T(1) : T(0)) + sm[(3 + 3 * d + c) * FQ + so] * sc[d];
+    const T J = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
+                F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
+                F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+    if (!(J > T(0))) atomicOr(err, 1);
+    T trC = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) trC += F[c][d] * F[c][d];
+    const T lnJ = log(J);
+    const T wdet = prm.tab.W[qx] * prm.tab.W[qy] * prm.tab.W[qz] * prm.detJ;
+    acc += wdet * (T(0.5) * prm.mu * (trC - T(3)) - prm.mu * lnJ + T(0.5) * prm.lam * lnJ * lnJ);
+  }
+  const double tot = block_sum(acc);
+  if (threadIdx.x == 0) partial[e] = tot;
+  if (last_block_done(counter)) {
+    const double s = ordered_sum(partial, gridDim.x);
+    if (threadIdx.x == 0) {
+      *out = s;
+      *counter = 0;
     }
   }
 }

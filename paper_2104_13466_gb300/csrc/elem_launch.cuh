@@ -98,6 +98,44 @@ cudaError_t launch_mass(const HostElemData& h, const double* x, double* y, cudaS
   return cudaGetLastError();
 }
 
+template <int P, typename T, typename TV>
+cudaError_t launch_mass_op(const HostElemData& h, double b1, const TV* x, TV* y, double* partial, PcgScalars* scal,
+                           cudaStream_t s) {
+  static bool init = false;
+  // the mass-only operator never touches the fourth shared field (Gz)
+  const size_t smem = sizeof(T) * 9 * Geo<P>::FQ;
+  if (!init) {
+    cudaError_t e = set_smem(tangent_kernel<P, T, TV, false>, smem);
+    if (e != cudaSuccess) return e;
+    init = true;
+  }
+  auto prm = make_params<T, P>(h, b1);
+  tangent_kernel<P, T, TV, false><<<h.nelem, elem_threads(P), smem, s>>>(prm, x, y, nullptr, partial, scal);
+  return cudaGetLastError();
+}
+
+template <int P, typename T>
+cudaError_t launch_mass_diag(const HostElemData& h, double b1, T* y, cudaStream_t s) {
+  auto prm = make_params<T, P>(h, b1);
+  mass_diag_kernel<P, T><<<h.nelem, 256, 0, s>>>(prm, y);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_energy(const HostElemData& h, const double* u, double* partial, unsigned int* counter,
+                          double* out, int* err, cudaStream_t s) {
+  static bool init = false;
+  const size_t smem = sizeof(double) * elem_smem_words<P>();
+  if (!init) {
+    cudaError_t e = set_smem(energy_kernel<P>, smem);
+    if (e != cudaSuccess) return e;
+    init = true;
+  }
+  auto prm = make_params<double, P>(h, 0.0);
+  energy_kernel<P><<<h.nelem, elem_threads(P), smem, s>>>(prm, u, partial, counter, out, err);
+  return cudaGetLastError();
+}
+
 #define SDME_INSTANTIATE_ORDER(P)                                                                     \
   template cudaError_t launch_residual<P>(const HostElemData&, double, const double*, double*, double*, \
                                           float*, int*, cudaStream_t);                                \
@@ -114,6 +152,14 @@ cudaError_t launch_mass(const HostElemData& h, const double* x, double* y, cudaS
                                               cudaStream_t);                                          \
   template cudaError_t launch_diag<P, float>(const HostElemData&, double, const float*, float*,        \
                                              cudaStream_t);                                           \
-  template cudaError_t launch_mass<P>(const HostElemData&, const double*, double*, cudaStream_t);
+  template cudaError_t launch_mass<P>(const HostElemData&, const double*, double*, cudaStream_t);           \
+  template cudaError_t launch_mass_op<P, double, double>(const HostElemData&, double, const double*, double*, \
+                                                         double*, PcgScalars*, cudaStream_t);              \
+  template cudaError_t launch_mass_op<P, float, float>(const HostElemData&, double, const float*, float*,    \
+                                                       double*, PcgScalars*, cudaStream_t);                \
+  template cudaError_t launch_mass_diag<P, double>(const HostElemData&, double, double*, cudaStream_t);      \
+  template cudaError_t launch_mass_diag<P, float>(const HostElemData&, double, float*, cudaStream_t);        \
+  template cudaError_t launch_energy<P>(const HostElemData&, const double*, double*, unsigned int*, double*, \
+                                        int*, cudaStream_t);
 
 }  // namespace sdme

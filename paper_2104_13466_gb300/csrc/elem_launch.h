@@ -35,5 +35,13 @@ template <int P, typename T>
 cudaError_t launch_diag(const HostElemData& h, double b1, const T* st, T* y, cudaStream_t s);
 template <int P>
 cudaError_t launch_mass(const HostElemData& h, const double* x, double* y, cudaStream_t s);
+template <int P, typename T, typename TV>
+cudaError_t launch_mass_op(const HostElemData& h, double b1, const TV* x, TV* y, double* partial, PcgScalars* scal,
+                           cudaStream_t s);
+template <int P, typename T>
+cudaError_t launch_mass_diag(const HostElemData& h, double b1, T* y, cudaStream_t s);
+template <int P>
+cudaError_t launch_energy(const HostElemData& h, const double* u, double* partial, unsigned int* counter,
+                          double* out, int* err, cudaStream_t s);
 
 }  // namespace sdme

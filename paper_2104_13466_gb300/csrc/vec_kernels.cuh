@@ -281,4 +281,64 @@ __global__ void __launch_bounds__(kVecThreads) k_to_double(int64_t n, const TV* 
     out[g] = scale * (double)x[g];
 }
 
+// Central-difference start-up (Sec. 4.1): u_prev = u0 - dt v0 + dt^2/2 a0 on
+// free DOFs, u0 on constrained ones.
+__global__ void __launch_bounds__(kVecThreads) k_cd_start(MeshInfo mi, const double* __restrict__ u,
+                                                          const double* __restrict__ v, const double* __restrict__ a,
+                                                          double dt, double* __restrict__ u_prev) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
+       g += (int64_t)gridDim.x * blockDim.x)
+    u_prev[g] = dof_constrained(mi, g) ? u[g] : u[g] - dt * v[g] + 0.5 * dt * dt * a[g];
+}
+
+// Central-difference update (eq. Motion_explicit2): out (holding u_{n-1})
+// <- 2 u_n - u_{n-1} + dt^2 a_n on free DOFs, u_n on constrained ones.
+__global__ void __launch_bounds__(kVecThreads) k_cd_update(MeshInfo mi, const double* __restrict__ u,
+                                                           const double* __restrict__ a, double dt2,
+                                                           double* __restrict__ u_prev) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const double un = u[g];
+    u_prev[g] = dof_constrained(mi, g) ? un : 2.0 * un - u_prev[g] + dt2 * a[g];
+  }
+}
+
+// out = x . y (float64, fixed-order finalize by the last CTA)
+__global__ void __launch_bounds__(kVecThreads) k_dot(int64_t n, const double* __restrict__ x,
+                                                     const double* __restrict__ y, double* __restrict__ partial,
+                                                     unsigned int* counter, double* out) {
+  double s = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    s += x[g] * y[g];
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  if (last_block_done(counter)) {
+    const double t = ordered_sum(partial, gridDim.x);
+    if (threadIdx.x == 0) {
+      *out = t;
+      *counter = 0;
+    }
+  }
+}
+
+// Deterministic pseudo-random start vector in [-1, 1] (integer hash of the
+// index), zero on constrained DOFs.
+__global__ void __launch_bounds__(kVecThreads) k_fill_hash(MeshInfo mi, double* __restrict__ x, unsigned seed) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)g * 2654435761u ^ seed;
+    h ^= h >> 16;
+    h *= 0x7feb352du;
+    h ^= h >> 15;
+    h *= 0x846ca68bu;
+    h ^= h >> 16;
+    x[g] = dof_constrained(mi, g) ? 0.0 : (double)h * (2.0 / 4294967295.0) - 1.0;
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) k_scale(int64_t n, double s, double* __restrict__ x) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    x[g] *= s;
+}
+
 }  // namespace sdme

@@ -1,0 +1,141 @@
+"""GPU parity of the explicit central-difference path (Sec. 4.1) against the oracle.
+
+Float64: 1e-10 relative (max-norm).  Mixed (float32 mass solve inside the
+float64 residual and state update): the float32 mass solve is converged to
+rtol 1e-6, so u_{n+1} differs from float64 by ~dt^2 |a| 1e-6 per step; the
+test bounds it at 1e-7 of |u| after a few steps.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import manufactured, solvers  # noqa: E402
+from oracle.assembly import Discretization  # noqa: E402
+from oracle.basis1d import Basis1D  # noqa: E402
+from oracle.hexmesh import BoxMesh  # noqa: E402
+from oracle.material import lame  # noqa: E402
+
+MU, LAM = lame(1000.0, 0.3)
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _pair(P, kind, prec=0, clamp=None, elems=(2, 2, 2)):
+    import paper_2104_13466_gb300 as s
+    clamp = clamp or {"xmin": (0, 1, 2)}
+    ctx = s.Context(elems, (1.0, 1.0, 1.0), clamp, MU, LAM, 1.0, P, kind, precision=prec)
+    mesh = BoxMesh(*elems, P)
+    for f, c in clamp.items():
+        mesh.clamp(f, c)
+    return ctx, Discretization(mesh, Basis1D(P, kind), MU, LAM, 1.0)
+
+
+def _fabricated_run(ctx, d, steps, dt, rtol):
+    fld = manufactured.sine_field()
+    n = d.mesh.ndof
+    v0 = d.l2_project(fld.velocity, 0.0)
+    v0[d.mask] = 0.0
+    loads = [manufactured.load_vector(d, fld, k * dt) for k in range(steps + 1)]
+    # oracle
+    u = np.zeros(n)
+    up, a = solvers.central_difference_start(d, u, v0, loads[0], dt)
+    Mm = solvers._masked_mass(d)
+    for k in range(steps):
+        un, a = solvers.central_difference_step(d, u, up, loads[k], dt, Mm=Mm)
+        up, u = u, un
+    # GPU
+    st = ctx.explicit_state(_dev(np.zeros(n)), _dev(np.zeros(n)), _dev(np.zeros(n)))
+    ctx.explicit_start(st, dt, _dev(loads[0]), _dev(v0), rtol=rtol)
+    its = []
+    for k in range(steps):
+        its.append(ctx.explicit_step(st, dt, _dev(loads[k]), rtol=rtol))
+    return (u, up, a), (_host(st.u), _host(st.u_prev), _host(st.a)), its
+
+
+@pytest.mark.parametrize("P,kind", [(2, "sdme_m"), (3, "sdme_m"), (4, "modal"), (3, "nodal")])
+def test_explicit_steps_fp64(P, kind):
+    ctx, d = _pair(P, kind)
+    (u, up, a), (ug, upg, ag), its = _fabricated_run(ctx, d, 6, 2e-4, 1e-13)
+    assert _rel(ug, u) < 1e-10 and _rel(upg, up) < 1e-10
+    # a_n comes from a PCG mass solve stopped at rtol 1e-13: its error is that
+    # times the condition number of the Jacobi-scaled mass matrix, ~1e5 for
+    # the modal basis at P = 4 and O(10) for the SDME and nodal bases
+    assert _rel(ag, a) < (1e-7 if kind == "modal" else 1e-9)
+    # the fabricated load vanishes at t = 0 (zero iterations); later steps iterate
+    assert its[0] == 0 and all(i > 0 for i in its[1:])
+
+
+def test_explicit_steps_mixed():
+    import paper_2104_13466_gb300 as s
+    ctx, d = _pair(3, "sdme_m", prec=s.MIXED_FP32)
+    (u, up, a), (ug, upg, ag), its = _fabricated_run(ctx, d, 6, 2e-4, 1e-6)
+    assert _rel(ug, u) < 1e-7
+    assert _rel(ag, a) < 1e-4
+
+
+def test_energy_matches_oracle():
+    ctx, d = _pair(3, "sdme_h")
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal(d.mesh.ndof) * 1e-3
+    v = rng.standard_normal(d.mesh.ndof)
+    ke, se = ctx.energy(_dev(u), _dev(v))
+    assert abs(ke - d.kinetic_energy(v)) < 1e-11 * abs(d.kinetic_energy(v))
+    assert abs(se - d.energy(u)) < 1e-10 * abs(d.energy(u))
+
+
+def test_dt_crit_estimate():
+    clamp = {f: (0, 1, 2) for f in ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")}
+    ctx, d = _pair(3, "sdme_m", clamp=clamp)
+    dt_gpu, lam_gpu = ctx.estimate_dt_crit(_dev(np.zeros(d.mesh.ndof)), iters=200)
+    free = ~d.mask
+    K = d.tangent_matrix(np.zeros(d.mesh.ndof), masked=False).toarray()[np.ix_(free, free)]
+    M = d.mass_matrix().toarray()[np.ix_(free, free)]
+    lmax = sla.eigh(K, M, eigvals_only=True)[-1]
+    # power iteration approaches lambda_max from below
+    assert 0.9 * lmax < lam_gpu <= lmax * (1 + 1e-9)
+    assert abs(dt_gpu - 2.0 / np.sqrt(lam_gpu)) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_explicit_energy_conservation(prec):
+    # no load, all faces clamped, sinusoidal initial velocity (config-2 shape)
+    clamp = {f: (0, 1, 2) for f in ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")}
+    ctx, d = _pair(3, "sdme_m", prec=prec, clamp=clamp)
+    n = d.mesh.ndof
+    v0 = d.l2_project(lambda X, t: np.stack([0 * X[..., 0], 0 * X[..., 0],
+                                              0.05 * np.sin(np.pi * X[..., 0]) * np.sin(np.pi * X[..., 1])
+                                              * np.sin(np.pi * X[..., 2])], axis=-1))
+    v0[d.mask] = 0.0
+    dt_crit, _ = ctx.estimate_dt_crit(_dev(np.zeros(n)), iters=100)
+    dt = 0.5 * dt_crit
+    zero = _dev(np.zeros(n))
+    st = ctx.explicit_state(_dev(np.zeros(n)), _dev(np.zeros(n)), _dev(np.zeros(n)))
+    ctx.explicit_start(st, dt, zero, _dev(v0), rtol=1e-12 if prec == 0 else 1e-6)
+    E0, _ = ctx.energy(v=_dev(v0))
+    E = []
+    prev = st.u_prev.clone()
+    for k in range(300):
+        ctx.explicit_step(st, dt, zero, rtol=1e-12 if prec == 0 else 1e-6)
+        # v_n = (u_{n+1} - u_{n-1}) / (2 dt), state now holds u_{n+1}, u_n
+        v = (st.u - prev) / (2 * dt)
+        ke, se = ctx.energy(st.u_prev, v.contiguous())
+        E.append(ke + se)
+        prev = st.u_prev.clone()
+    E = np.array(E)
+    assert np.abs(E - E0).max() < 0.02 * E0
+    q = len(E) // 4
+    assert abs(E[-q:].mean() - E[:q].mean()) < 2e-3 * E0
