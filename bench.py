@@ -410,6 +410,70 @@ def run_compare(args, w):
             ctx.close()
 
 
+def run_explicit(args, w):
+    """Explicit central-difference run (config 2 shape): v0 projected from the
+    seeded sinusoidal field, dt = 0.5 dt_crit from a power iteration, N steps
+    without load in float64 and in mixed precision on identical inputs;
+    reports time per step, energy drift and the mixed-vs-float64 difference.
+    The configuration is the unit cube (nx = ny = nz) with all faces clamped."""
+    import torch
+    import paper_2104_13466_gb300 as sd
+    from synthetic import random_uniform
+    mu, lam = lame(w["E"], w["nu"])
+    amp = w["v_amp"] * (1.0 + 0.01 * float(random_uniform(1, w["seed"])[0]))
+    out = {"mode": "explicit", "workload": args.workload, "basis": args.basis, "amplitude": amp}
+    v0 = None
+    results = {}
+    for prec_name in ("fp64", "mixed"):
+        prec = sd.MIXED_FP32 if prec_name == "mixed" else sd.FP64
+        ctx = sd.Context(w["elems"], w["lengths"], w["clamp"], mu, lam, w["rho"], w["P"], args.basis,
+                         precision=prec)
+        n = ctx.ndof
+        if v0 is None:
+            # L2 projection of v0 = A sin(pi x) sin(pi y) sin(pi z) e_z (float64 context)
+            X = ctx.gauss_point_coords(w["elems"], w["lengths"]).cuda()
+            fq = torch.zeros(X.shape[0], 3, X.shape[1], dtype=torch.float64, device="cuda")
+            fq[:, 2, :] = amp * torch.sin(np.pi * X[..., 0]) * torch.sin(np.pi * X[..., 1]) * \
+                torch.sin(np.pi * X[..., 2])
+            b = torch.zeros(n, dtype=torch.float64, device="cuda")
+            ctx.body_load(fq.contiguous(), b)
+            v0 = torch.zeros_like(b)
+            ctx.mass_solve(b, v0, rtol=1e-13)
+            dt_crit, lam_max = ctx.estimate_dt_crit(torch.zeros_like(b), iters=args.dt_iters)
+            dt = w["cfl"] * dt_crit
+            out.update({"dt_crit": dt_crit, "dt": dt, "ndof": n})
+        zero = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st = ctx.explicit_state(torch.zeros_like(zero), torch.zeros_like(zero), torch.zeros_like(zero))
+        rtol = w["mass_rtol"] if prec == sd.FP64 else w["mass_rtol_mixed"]
+        ctx.explicit_start(st, dt, zero, v0, rtol=rtol)
+        E0, _ = ctx.energy(v=v0)
+        energies, its_total = [], 0
+        torch.cuda.synchronize()
+        t_ms = 0.0
+        prev = st.u_prev.clone()
+        for k in range(1, args.explicit_steps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            its_total += ctx.explicit_step(st, dt, zero, rtol=rtol)
+            e1.record()
+            torch.cuda.synchronize()
+            t_ms += e0.elapsed_time(e1)
+            if k % args.energy_every == 0:
+                v = ((st.u - prev) / (2 * dt)).contiguous()
+                ke, se = ctx.energy(st.u_prev, v)
+                energies.append((k, (ke + se) / E0 - 1.0))
+            prev.copy_(st.u_prev)
+        results[prec_name] = {"u": st.u.clone(), "ms_per_step": t_ms / args.explicit_steps,
+                              "mass_pcg_iters_per_step": its_total / args.explicit_steps,
+                              "energy_rel_dev_max": max(abs(e) for _, e in energies),
+                              "energy_rel_dev_last": energies[-1][1], "energy_trace": energies[::5]}
+        ctx.close()
+    u64, u32 = results["fp64"].pop("u"), results["mixed"].pop("u")
+    out["mixed_vs_fp64_u_rel"] = float(torch.linalg.norm(u32 - u64) / torch.linalg.norm(u64))
+    out["fp64"], out["mixed"] = results["fp64"], results["mixed"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -427,6 +491,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-only", action="store_true")
     ap.add_argument("--compare", action="store_true")
+    ap.add_argument("--explicit", action="store_true")
+    ap.add_argument("--explicit-steps", type=int, default=2000)
+    ap.add_argument("--energy-every", type=int, default=50)
+    ap.add_argument("--dt-iters", type=int, default=100)
     ap.add_argument("--bases", default="nodal,modal,sdme_m,sdme_h")
     ap.add_argument("--precisions", default="mixed,fp64")
     ap.add_argument("--kernel-iters", type=int, default=20)
@@ -436,6 +504,8 @@ def main():
         run_kernel_only(args, w)
     elif args.compare:
         run_compare(args, w)
+    elif args.explicit:
+        run_explicit(args, w)
     elif args.impl == "reference":
         run_reference(args, w)
     else:

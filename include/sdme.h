@@ -253,6 +253,26 @@ sdme_status sdme_energy(sdme_ctx* ctx, const double* u_dev, const double* v_dev,
 sdme_status sdme_estimate_dt_crit(sdme_ctx* ctx, const double* u_dev, int iters, double* dt_crit,
                                   double* lambda_max);
 
+/*
+ * Body load f_dev = int N_i f dV (third term of eq. material virtual work,
+ * f per unit reference volume) from f sampled at the Gauss points:
+ * fq_dev[(e*3 + c)*Q^3 + q], element e = (ez ny + ey) nx + ex, component c,
+ * Gauss point q = (k3 Q + k2) Q + k1 at reference coordinates
+ * (xq[k1], xq[k2], xq[k3]) (sdme_gauss_points), Q = P + 2.  Overwrites f_dev.
+ */
+sdme_status sdme_body_load(sdme_ctx* ctx, const double* fq_dev, double* f_dev);
+
+/*
+ * Solve M x = b (consistent mass, constrained rows identity, b's constrained
+ * entries ignored) by Jacobi-PCG from zero to ||r|| <= rtol ||b||, in the
+ * context's precision; e.g. the L2 projection of an initial field.
+ */
+sdme_status sdme_mass_solve(sdme_ctx* ctx, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters,
+                            double* final_rel);
+
+/* The context's Q = P + 2 Gauss-Legendre points and weights on [-1, 1] (host arrays, may be NULL). */
+sdme_status sdme_gauss_points(const sdme_ctx* ctx, double* xq, double* wq);
+
 /* Cumulative device event timings of the context (ms) and counts, for measurement. */
 typedef struct {
   double tangent_ms;     /* sum of timed tangent-kernel launches */

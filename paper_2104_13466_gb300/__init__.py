@@ -31,7 +31,7 @@ EXPORTS = ("sdme_status_string", "sdme_build_basis1d", "sdme_create", "sdme_dest
            "sdme_internal_force", "sdme_mass_apply", "sdme_tangent_apply", "sdme_diagonal", "sdme_pcg_solve",
            "sdme_traction_load", "sdme_implicit_newmark_step", "sdme_set_timing", "sdme_get_timing",
            "sdme_tangent_apply_noalloc", "sdme_cuda_error_string", "sdme_explicit_start", "sdme_explicit_step",
-           "sdme_energy", "sdme_estimate_dt_crit")
+           "sdme_energy", "sdme_estimate_dt_crit", "sdme_body_load", "sdme_mass_solve", "sdme_gauss_points")
 
 
 class BasisDesc(ctypes.Structure):
@@ -103,6 +103,9 @@ def _load():
     lib.sdme_explicit_step.argtypes = [vp, ctypes.POINTER(ExplicitState), d, vp, d, i, ctypes.POINTER(i)]
     lib.sdme_energy.argtypes = [vp, vp, vp, pd, pd]
     lib.sdme_estimate_dt_crit.argtypes = [vp, vp, i, pd, pd]
+    lib.sdme_body_load.argtypes = [vp, vp, vp]
+    lib.sdme_mass_solve.argtypes = [vp, vp, vp, d, i, ctypes.POINTER(i), pd]
+    lib.sdme_gauss_points.argtypes = [vp, pd, pd]
     lib.sdme_set_timing.argtypes = [vp, i]
     lib.sdme_get_timing.argtypes = [vp, ctypes.POINTER(Timing)]
     lib.sdme_tangent_apply_noalloc.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(Material), i, pd, pd, pd,
@@ -189,7 +192,7 @@ def tangent_apply_noalloc(elems, lengths, clamp, mu, lam, rho, P, tables, u, b1,
     return _check(lib.sdme_tangent_apply_noalloc(ctypes.byref(mesh), ctypes.byref(mat), int(P), *ptrs, _ptr(u),
                                                  float(b1), _ptr(x), _ptr(y), ctypes.c_void_p(stream.cuda_stream)),
                   "sdme_tangent_apply_noalloc", "sdme_cuda_error_string", "sdme_explicit_start", "sdme_explicit_step",
-           "sdme_energy", "sdme_estimate_dt_crit")
+           "sdme_energy", "sdme_estimate_dt_crit", "sdme_body_load", "sdme_mass_solve", "sdme_gauss_points")
 
 
 class _ExplicitStateHolder:
@@ -317,6 +320,39 @@ class Context:
         _check(lib.sdme_estimate_dt_crit(self._h, _ptr(u), int(iters), ctypes.byref(dt), ctypes.byref(lam)),
                "sdme_estimate_dt_crit", ctx=self._h)
         return dt.value, lam.value
+
+    def gauss_points(self):
+        import numpy as np
+        Q = self.P + 2
+        xq, wq = np.zeros(Q), np.zeros(Q)
+        _check(lib.sdme_gauss_points(self._h, xq.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     wq.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "sdme_gauss_points")
+        return xq, wq
+
+    def gauss_point_coords(self, elems, lengths):
+        """Physical coordinates (torch, float64, [nelem][Q^3][3]) of the Gauss
+        points in the layout sdme_body_load expects (host-side helper)."""
+        import numpy as np
+        import torch
+        xq, _ = self.gauss_points()
+        Q = self.P + 2
+        h = [lengths[d] / elems[d] for d in range(3)]
+        k3, k2, k1 = np.meshgrid(np.arange(Q), np.arange(Q), np.arange(Q), indexing="ij")
+        ref = np.stack([xq[k1.ravel()], xq[k2.ravel()], xq[k3.ravel()]], axis=-1)     # (Q3, 3)
+        ez, ey, ex = np.meshgrid(np.arange(elems[2]), np.arange(elems[1]), np.arange(elems[0]), indexing="ij")
+        org = np.stack([ex.ravel() * h[0], ey.ravel() * h[1], ez.ravel() * h[2]], axis=-1)  # (E, 3)
+        X = org[:, None, :] + 0.5 * (1.0 + ref[None, :, :]) * np.array(h)[None, None, :]
+        return torch.from_numpy(X)
+
+    def body_load(self, fq, f):
+        return _check(lib.sdme_body_load(self._h, _ptr(fq), _ptr(f)), "sdme_body_load", ctx=self._h)
+
+    def mass_solve(self, b, x, rtol=1e-12, maxit=20000):
+        its = ctypes.c_int()
+        rel = ctypes.c_double()
+        _check(lib.sdme_mass_solve(self._h, _ptr(b), _ptr(x), float(rtol), int(maxit), ctypes.byref(its),
+                                   ctypes.byref(rel)), "sdme_mass_solve", ctx=self._h)
+        return its.value, rel.value
 
     def set_timing(self, enable=True):
         return _check(lib.sdme_set_timing(self._h, int(bool(enable))), "sdme_set_timing")

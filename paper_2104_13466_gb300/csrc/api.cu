@@ -772,6 +772,33 @@ sdme_status sdme_estimate_dt_crit(sdme_ctx* ctx, const double* u_dev, int iters,
   return SDME_OK;
 }
 
+sdme_status sdme_body_load(sdme_ctx* ctx, const double* fq_dev, double* f_dev) {
+  if (!ctx || !fq_dev || !f_dev) return SDME_EINVAL;
+  SDME_CUDA(cudaMemsetAsync(f_dev, 0, sizeof(double) * ctx->ndof, ctx->stream));
+  SDME_CUDA(dispatch_P(ctx->h.P, [&](auto Pc) {
+    return launch_body_load<decltype(Pc)::value>(ctx->h, fq_dev, f_dev, ctx->stream);
+  }));
+  ctx->kernel_launches += 1;
+  return SDME_OK;
+}
+
+sdme_status sdme_mass_solve(sdme_ctx* ctx, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters,
+                            double* final_rel) {
+  if (!ctx || !b_dev || !x_dev || maxit < 1 || !(rtol >= 0.0)) return SDME_EINVAL;
+  return pcg_dispatch(ctx, 1.0, b_dev, x_dev, rtol, maxit, iters, final_rel, true);
+}
+
+sdme_status sdme_gauss_points(const sdme_ctx* ctx, double* xq, double* wq) {
+  if (!ctx) return SDME_EINVAL;
+  std::vector<double> x(ctx->Q), w(ctx->Q);
+  gauss_legendre(ctx->Q, x.data(), w.data());
+  for (int q = 0; q < ctx->Q; ++q) {
+    if (xq) xq[q] = x[q];
+    if (wq) wq[q] = w[q];
+  }
+  return SDME_OK;
+}
+
 const char* sdme_cuda_error_string(const sdme_ctx* ctx) {
   if (!ctx) return "no context";
   return cudaGetErrorString(ctx->last_cuda != cudaSuccess ? ctx->last_cuda : ctx->last_timing_error);

@@ -738,4 +738,39 @@ energy_kernel(const __grid_constant__ ElemParams<double, P> prm, const double* _
   }
 }
 
+//-----------------------------------------------------------------------------
+// Body load: y += int N_m f_c dV with f given at the Gauss points,
+// fq[e][c][q] (third term of eq. material virtual work, per unit reference
+// volume).  No Dirichlet treatment.
+//-----------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(elem_threads(P))
+body_load_kernel(const __grid_constant__ ElemParams<double, P> prm, const double* __restrict__ fq,
+                 double* __restrict__ y) {
+  using T = double;
+  using G = Geo<P>;
+  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* X = sm + 3 * FQ;
+  const int e = blockIdx.x;
+  const ElemView<ElemParams<double, P>> view(prm, P, e);
+  const double* fe = fq + (int64_t)e * 3 * Q3;
+  for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
+    const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
+    const int so = (qz * Q + qy) * XQ + qx;
+    const T wdet = prm.tab.W[qx] * prm.tab.W[qy] * prm.tab.W[qz] * prm.detJ;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sm[c * FQ + so] = wdet * fe[c * Q3 + q];
+  }
+  __syncthreads();
+  transpose_stages<T, P, false>(prm.tab, sm);
+  for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
+    bool cons;
+    int so;
+    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
+    atomicAdd(&y[g], X[so]);
+  }
+}
+
 }  // namespace sdme

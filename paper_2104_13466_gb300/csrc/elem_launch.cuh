@@ -136,6 +136,20 @@ cudaError_t launch_energy(const HostElemData& h, const double* u, double* partia
   return cudaGetLastError();
 }
 
+template <int P>
+cudaError_t launch_body_load(const HostElemData& h, const double* fq, double* y, cudaStream_t s) {
+  static bool init = false;
+  const size_t smem = sizeof(double) * elem_smem_words<P>();
+  if (!init) {
+    cudaError_t e = set_smem(body_load_kernel<P>, smem);
+    if (e != cudaSuccess) return e;
+    init = true;
+  }
+  auto prm = make_params<double, P>(h, 0.0);
+  body_load_kernel<P><<<h.nelem, elem_threads(P), smem, s>>>(prm, fq, y);
+  return cudaGetLastError();
+}
+
 #define SDME_INSTANTIATE_ORDER(P)                                                                     \
   template cudaError_t launch_residual<P>(const HostElemData&, double, const double*, double*, double*, \
                                           float*, int*, cudaStream_t);                                \
@@ -160,6 +174,7 @@ cudaError_t launch_energy(const HostElemData& h, const double* u, double* partia
   template cudaError_t launch_mass_diag<P, double>(const HostElemData&, double, double*, cudaStream_t);      \
   template cudaError_t launch_mass_diag<P, float>(const HostElemData&, double, float*, cudaStream_t);        \
   template cudaError_t launch_energy<P>(const HostElemData&, const double*, double*, unsigned int*, double*, \
-                                        int*, cudaStream_t);
+                                        int*, cudaStream_t);                                                \
+  template cudaError_t launch_body_load<P>(const HostElemData&, const double*, double*, cudaStream_t);
 
 }  // namespace sdme

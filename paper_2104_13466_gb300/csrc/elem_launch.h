@@ -41,6 +41,8 @@ cudaError_t launch_mass_op(const HostElemData& h, double b1, const TV* x, TV* y,
 template <int P, typename T>
 cudaError_t launch_mass_diag(const HostElemData& h, double b1, T* y, cudaStream_t s);
 template <int P>
+cudaError_t launch_body_load(const HostElemData& h, const double* fq, double* y, cudaStream_t s);
+template <int P>
 cudaError_t launch_energy(const HostElemData& h, const double* u, double* partial, unsigned int* counter,
                           double* out, int* err, cudaStream_t s);
 

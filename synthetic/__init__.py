@@ -16,6 +16,9 @@ lambda = 100) scaled to the GPU problem sizes:
                 x = 0 clamped, dead shear traction on x = 8 ramped over 20 steps.
 * ``beam_p8_dyn``  the same cantilever with dt = 3e-4, the paper's ratio of
                 time step to element wave-transit time (mass-dominated steps).
+* ``cube_p6_explicit``  explicit central-difference run on the unit cube,
+                16^3 hexes, P = 6 (2.74 M DOFs), all faces clamped, seeded
+                sinusoidal initial velocity, 2000 steps at half the stable step.
 * ``static_fab``  the paper's static fabricated problem (Sec. 5.1): unit cube,
                 2x2x2 hexes, x = 0 clamped.
 
@@ -50,6 +53,14 @@ WORKLOADS = {
         clamp={"xmin": (0, 1, 2)}, traction_face="xmax", traction_dir=(0.0, 0.0, -1.0),
         steps=20, dt=3.0e-4, newton_tol=1e-8, pcg_rtol=1e-10, k=0.5, lam=100.0,
         load_key="beam_traction"),
+    # explicit elastodynamics: unit cube of 16^3 hexes at P = 6, all faces
+    # clamped, initial velocity v_amp (1 + 0.01 xi) sin(pi x) sin(pi y)
+    # sin(pi z) e_z with xi ~ U(-1, 1) drawn from `seed`, no load, steps at
+    # cfl x the critical step
+    "cube_p6_explicit": dict(
+        elems=(16, 16, 16), P=6, lengths=(1.0, 1.0, 1.0), E=1.0e3, nu=0.3, rho=1.0,
+        clamp={f: (0, 1, 2) for f in ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")},
+        v_amp=0.05, seed=0, cfl=0.5, steps=2000, mass_rtol=1e-12, mass_rtol_mixed=1e-6),
     "static_fab": dict(
         elems=(2, 2, 2), P=4, lengths=(1.0, 1.0, 1.0), E=1.0e3, nu=0.3, rho=1.0,
         clamp={"xmin": (0, 1, 2)}, k=0.5, lam=100.0),

@@ -36,7 +36,7 @@ def _rel(a, b):
 
 def _pair(P, kind, prec=0, clamp=None, elems=(2, 2, 2)):
     import paper_2104_13466_gb300 as s
-    clamp = clamp or {"xmin": (0, 1, 2)}
+    clamp = {"xmin": (0, 1, 2)} if clamp is None else clamp
     ctx = s.Context(elems, (1.0, 1.0, 1.0), clamp, MU, LAM, 1.0, P, kind, precision=prec)
     mesh = BoxMesh(*elems, P)
     for f, c in clamp.items():
@@ -139,3 +139,21 @@ def test_explicit_energy_conservation(prec):
     assert np.abs(E - E0).max() < 0.02 * E0
     q = len(E) // 4
     assert abs(E[-q:].mean() - E[:q].mean()) < 2e-3 * E0
+
+
+def test_body_load_and_l2_projection():
+    ctx, d = _pair(4, "sdme_m", clamp={})
+    elems, lengths = (2, 2, 2), (1.0, 1.0, 1.0)
+
+    def func(X, t=0.0):
+        return np.stack([np.sin(X[..., 0]), X[..., 0] * X[..., 1], X[..., 2] ** 2], axis=-1)
+
+    Xq = ctx.gauss_point_coords(elems, lengths).numpy()                  # (E, Q3, 3)
+    fq = np.ascontiguousarray(func(Xq).transpose(0, 2, 1))                # (E, 3, Q3)
+    f = torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda")
+    ctx.body_load(_dev(fq.ravel()), f)
+    want = d.body_load(func)
+    assert _rel(_host(f), want) < 1e-12
+    x = torch.zeros_like(f)
+    its, rel = ctx.mass_solve(f, x, rtol=1e-13)
+    assert _rel(_host(x), d.l2_project(func)) < 1e-10
