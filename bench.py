@@ -39,14 +39,22 @@ def lame(E, nu):
     return E / (2.0 * (1.0 + nu)), E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
 
 
-def tangent_flops_per_element(P):
-    """Algorithmic float ops of one element's tangent action, as the kernel
-    computes it: 3 components x (interpolation n^3Q + n^2Q^2 + nQ^3 +
-    collocated derivatives 3 Q^4) multiply-adds, forward and transposed, plus
-    207 flops of pointwise linearised stress per Gauss point."""
+def tangent_flops_per_element(P, nodal=False):
+    """Float ops of one element's tangent action as the kernel computes it,
+    with the even-odd (mirror) split of every 1D contraction.  Per line:
+    interpolation between n modes and Q points 2 (QH n + [Q odd] NE) + 2 QH + 2,
+    collocated derivative 2 (2 QH^2 + [Q odd] 2 QH) + 4 QH, the same for the
+    transposed forms; a nodal basis adds n - 2 pairing adds per mode-side
+    line.  Lines per component and direction: n^2 + nQ + Q^2 interpolations
+    and 3 Q^2 derivatives; 207 flops of pointwise linearised stress per Gauss
+    point.  (The plain contraction count, 4 x 3 (n^3 Q + n^2 Q^2 + n Q^3 +
+    3 Q^4) + 207 Q^3, is 1.46x this at P = 8.)"""
     n, Q = P + 1, P + 2
-    mac = 3 * (n ** 3 * Q + n ** 2 * Q ** 2 + n * Q ** 3 + 3 * Q ** 4)
-    return 2 * 2 * mac + 207 * Q ** 3
+    QH, NE, odd = Q // 2, 1 + P // 2, Q % 2
+    interp = 2 * (QH * n + odd * NE) + 2 * QH + 2 + (n - 2 if nodal else 0)
+    deriv = 2 * (2 * QH * QH + odd * 2 * QH) + 4 * QH
+    per_dir = (n * n + n * Q + Q * Q) * interp + 3 * Q * Q * deriv
+    return 3 * 2 * per_dir + 207 * Q ** 3
 
 
 def tangent_bytes(P, nelem, ndof, word_state, word_vec):
@@ -270,7 +278,7 @@ def run_gpu(args, w):
     tan_launches = t1["tangent_launches"] - t0["tangent_launches"]
     avg_tan = tan_ms / max(1, tan_launches)
     wstate = 4 if prec == sd.MIXED_FP32 else 8
-    flops = tangent_flops_per_element(w["P"]) * ctx.nelem
+    flops = tangent_flops_per_element(w["P"], args.basis == "nodal") * ctx.nelem
     nbytes = tangent_bytes(w["P"], ctx.nelem, n, wstate, wstate)
     achieved_tf = flops / (avg_tan * 1e-3) / 1e12
     alu_peak = FP32_PEAK_TFLOPS if prec == sd.MIXED_FP32 else FP64_PEAK_TFLOPS
@@ -356,7 +364,7 @@ def run_kernel_only(args, w):
     its, rel = ctx.pcg_solve(u, 4.0, b, x, rtol=0.0, maxit=args.kernel_iters, allow_maxit=True)
     t = ctx.timing()
     avg = t["tangent_ms"] / max(1, t["tangent_launches"])
-    flops = tangent_flops_per_element(w["P"]) * ctx.nelem
+    flops = tangent_flops_per_element(w["P"], args.basis == "nodal") * ctx.nelem
     print(json.dumps({"mode": "kernel-only", "precision": args.precision, "basis": args.basis, "iters": its,
                       "tangent_avg_ms": avg, "tflops": flops / (avg * 1e-3) / 1e12, "launches": t["tangent_launches"]}),
           flush=True)

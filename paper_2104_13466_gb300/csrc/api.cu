@@ -13,6 +13,7 @@
 #include "basis1d.h"
 #include "common.cuh"
 #include "elem_launch.h"
+#include "eo_tables.h"
 #include "vec_kernels.cuh"
 
 using namespace sdme;
@@ -437,6 +438,23 @@ sdme_status sdme_create(sdme_ctx** out, const sdme_mesh_desc* mesh, const sdme_m
   gauss_legendre(Q, xq.data(), h.W.data());
   b.tables(Q, xq.data(), h.B.data(), h.D.data());
   collocation_derivative(Q, xq.data(), h.DQ.data());
+  {
+    const EoSizes z(P);
+    h.TE.resize(z.QH * z.NE);
+    h.TO.resize(z.QH * z.NO);
+    h.TEm.resize(z.NE);
+    h.AH.resize(z.QH * z.QH);
+    h.CH.resize(z.QH * z.QH);
+    h.CM.resize(z.QH);
+    h.DM.resize(z.QH);
+    const int sym = build_eo_tables(P, h.B.data(), h.DQ.data(), h.TE.data(), h.TO.data(), h.TEm.data(),
+                                    h.AH.data(), h.CH.data(), h.CM.data(), h.DM.data());
+    if (sym == kEoNone) {  // e.g. a modal basis with jacobi_alpha != jacobi_beta
+      delete ctx;
+      return SDME_EUNSUPPORTED;
+    }
+    h.pairs = sym == kEoNodalPairs ? 1 : 0;
+  }
   double hh[3];
   for (int d = 0; d < 3; ++d) {
     hh[d] = mesh->length[d] / mesh->nelem[d];

@@ -28,10 +28,20 @@ template <typename T, int P>
 struct ElemTables {
   static constexpr int n = P + 1;
   static constexpr int Q = P + 2;
-  T B[Q * n];   // B[q*n + p] = phi_p(xi_q), lattice order
-  T D[Q * n];   // D[q*n + p] = phi_p'(xi_q)
-  T DQ[Q * Q];  // DQ[q*Q + m] = l_m'(xi_q), Lagrange through the Gauss points
-  T W[Q];       // Gauss weights
+  static constexpr int QH = Q / 2;          // mirror pairs of Gauss points
+  static constexpr int NE = 1 + P / 2;      // even / odd mode counts (canonical structure)
+  static constexpr int NO = 1 + (P - 1) / 2;
+  T B[Q * n];     // B[q*n + p] = phi_p(xi_q), lattice order (diagonal kernels)
+  T D[Q * n];     // D[q*n + p] = phi_p'(xi_q)
+  T W[Q];         // Gauss weights
+  // even-odd half tables (see eo_tables.h)
+  T TE[QH * NE];
+  T TO[QH * NO];
+  T TEm[NE];
+  T AH[QH * QH];
+  T CH[QH * QH];
+  T CM[QH];
+  T DM[QH];
 };
 
 template <typename T, int P>
@@ -45,7 +55,185 @@ struct ElemParams {
   int N[3];      // lattice points per direction
   int64_t Nn;    // lattice points (per component)
   unsigned clamp[6];
+  int pairs;     // 1: nodal basis, pair mirrored internal nodes on the fly
 };
+
+//-----------------------------------------------------------------------------
+// Even-odd line contractions.  `in`/`out` are register arrays; all loops are
+// unrolled so every table entry is a compile-time offset in the parameter
+// block.  Mode-side vectors are in the canonical structure (eo_tables.h).
+//-----------------------------------------------------------------------------
+// nodal values -> canonical coefficients: c_e = u_i + u_j, c_o = u_i - u_j
+template <typename T, int n>
+__device__ __forceinline__ void to_canonical(T (&v)[n]) {
+  constexpr int np = (n - 2) / 2;
+  T t[n];
+#pragma unroll
+  for (int i = 0; i < n; ++i) t[i] = v[i];
+#pragma unroll
+  for (int i = 1; i <= np; ++i) {
+    v[2 * i - 1] = t[i] + t[n - 1 - i];
+    v[2 * i] = t[i] - t[n - 1 - i];
+  }
+  if ((n - 2) % 2 == 1) v[n - 2] = t[(n - 1) / 2];
+}
+
+// canonical results -> nodal results: r_i = r_e + r_o, r_j = r_e - r_o
+template <typename T, int n>
+__device__ __forceinline__ void from_canonical(T (&v)[n]) {
+  constexpr int np = (n - 2) / 2;
+  T t[n];
+#pragma unroll
+  for (int i = 0; i < n; ++i) t[i] = v[i];
+#pragma unroll
+  for (int i = 1; i <= np; ++i) {
+    v[i] = t[2 * i - 1] + t[2 * i];
+    v[n - 1 - i] = t[2 * i - 1] - t[2 * i];
+  }
+  if ((n - 2) % 2 == 1) v[(n - 1) / 2] = t[n - 2];
+}
+
+// out[q] = sum_j B[q][j] in[j] (modes -> Gauss points)
+template <typename T, int P>
+__device__ __forceinline__ void eo_interp(const ElemTables<T, P>& tb, const T (&in)[P + 1], T (&out)[P + 2]) {
+  using E = ElemTables<T, P>;
+  constexpr int n = E::n, Q = E::Q, QH = E::QH, NE = E::NE, NO = E::NO;
+  T e[NE], o[NO];
+  e[0] = in[0] + in[n - 1];
+  o[0] = in[0] - in[n - 1];
+#pragma unroll
+  for (int k = 1; k < NE; ++k) e[k] = in[2 * k - 1];
+#pragma unroll
+  for (int k = 1; k < NO; ++k) o[k] = in[2 * k];
+#pragma unroll
+  for (int q = 0; q < QH; ++q) {
+    T S = T(0), D = T(0);
+#pragma unroll
+    for (int k = 0; k < NE; ++k) S += tb.TE[q * NE + k] * e[k];
+#pragma unroll
+    for (int k = 0; k < NO; ++k) D += tb.TO[q * NO + k] * o[k];
+    out[q] = S + D;
+    out[Q - 1 - q] = S - D;
+  }
+  if (Q % 2 == 1) {
+    T M = T(0);
+#pragma unroll
+    for (int k = 0; k < NE; ++k) M += tb.TEm[k] * e[k];
+    out[QH] = M;
+  }
+}
+
+// out[j] = sum_q B[q][j] in[q] (Gauss points -> modes)
+template <typename T, int P>
+__device__ __forceinline__ void eo_interp_t(const ElemTables<T, P>& tb, const T (&in)[P + 2], T (&out)[P + 1]) {
+  using E = ElemTables<T, P>;
+  constexpr int n = E::n, Q = E::Q, QH = E::QH, NE = E::NE, NO = E::NO;
+  T sv[QH], dv[QH];
+#pragma unroll
+  for (int q = 0; q < QH; ++q) {
+    sv[q] = in[q] + in[Q - 1 - q];
+    dv[q] = in[q] - in[Q - 1 - q];
+  }
+  T ee[NE], oo[NO];
+#pragma unroll
+  for (int k = 0; k < NE; ++k) {
+    T a = (Q % 2 == 1) ? tb.TEm[k] * in[QH] : T(0);
+#pragma unroll
+    for (int q = 0; q < QH; ++q) a += tb.TE[q * NE + k] * sv[q];
+    ee[k] = a;
+  }
+#pragma unroll
+  for (int k = 0; k < NO; ++k) {
+    T a = T(0);
+#pragma unroll
+    for (int q = 0; q < QH; ++q) a += tb.TO[q * NO + k] * dv[q];
+    oo[k] = a;
+  }
+  out[0] = ee[0] + oo[0];
+  out[n - 1] = ee[0] - oo[0];
+#pragma unroll
+  for (int k = 1; k < NE; ++k) out[2 * k - 1] = ee[k];
+#pragma unroll
+  for (int k = 1; k < NO; ++k) out[2 * k] = oo[k];
+}
+
+// out[q] = sum_m DQ[q][m] u[m] (collocated derivative on the Gauss points)
+template <typename T, int P>
+__device__ __forceinline__ void eo_deriv(const ElemTables<T, P>& tb, const T (&u)[P + 2], T (&out)[P + 2]) {
+  using E = ElemTables<T, P>;
+  constexpr int Q = E::Q, QH = E::QH;
+  T su[QH], du[QH];
+#pragma unroll
+  for (int m = 0; m < QH; ++m) {
+    su[m] = u[m] + u[Q - 1 - m];
+    du[m] = u[m] - u[Q - 1 - m];
+  }
+#pragma unroll
+  for (int q = 0; q < QH; ++q) {
+    T X = T(0), Y = (Q % 2 == 1) ? tb.CM[q] * u[QH] : T(0);
+#pragma unroll
+    for (int m = 0; m < QH; ++m) {
+      X += tb.AH[q * QH + m] * du[m];
+      Y += tb.CH[q * QH + m] * su[m];
+    }
+    out[q] = X + Y;
+    out[Q - 1 - q] = X - Y;
+  }
+  if (Q % 2 == 1) {
+    T M = T(0);
+#pragma unroll
+    for (int m = 0; m < QH; ++m) M += tb.DM[m] * du[m];
+    out[QH] = M;
+  }
+}
+
+// out[m] = sum_q DQ[q][m] g[q] (transposed collocated derivative)
+template <typename T, int P>
+__device__ __forceinline__ void eo_deriv_t(const ElemTables<T, P>& tb, const T (&g)[P + 2], T (&out)[P + 2]) {
+  using E = ElemTables<T, P>;
+  constexpr int Q = E::Q, QH = E::QH;
+  T sg[QH], dg[QH];
+#pragma unroll
+  for (int q = 0; q < QH; ++q) {
+    sg[q] = g[q] + g[Q - 1 - q];
+    dg[q] = g[q] - g[Q - 1 - q];
+  }
+#pragma unroll
+  for (int m = 0; m < QH; ++m) {
+    T X = T(0), Y = (Q % 2 == 1) ? tb.DM[m] * g[QH] : T(0);
+#pragma unroll
+    for (int q = 0; q < QH; ++q) {
+      X += tb.CH[q * QH + m] * dg[q];
+      Y += tb.AH[q * QH + m] * sg[q];
+    }
+    out[m] = X + Y;
+    out[Q - 1 - m] = X - Y;
+  }
+  if (Q % 2 == 1) {
+    T M = T(0);
+#pragma unroll
+    for (int q = 0; q < QH; ++q) M += tb.CM[q] * dg[q];
+    out[QH] = M;
+  }
+}
+
+template <int N, typename T>
+__device__ __forceinline__ void load_line(const T* s, int stride, T (&v)[N]) {
+#pragma unroll
+  for (int a = 0; a < N; ++a) v[a] = s[a * stride];
+}
+
+template <int N, typename T>
+__device__ __forceinline__ void store_line(T* d, int stride, const T (&v)[N]) {
+#pragma unroll
+  for (int a = 0; a < N; ++a) d[a * stride] = v[a];
+}
+
+template <int N, typename T>
+__device__ __forceinline__ void add_line(T* d, int stride, const T (&v)[N]) {
+#pragma unroll
+  for (int a = 0; a < N; ++a) d[a * stride] += v[a];
+}
 
 // Lattice point on a clamped face for component c?
 template <typename Prm>
@@ -104,23 +292,6 @@ constexpr int elem_smem_words() {
   return Geo<P>::WORDS;
 }
 
-// One line contraction: out[b] (+)= sum_a M(b, a) in[a] with
-// M(b, a) = TR ? Mt[a*NO + b] : Mt[b*NI + a]; source / destination element
-// strides si / so.
-template <int NI, int NO, bool TR, bool ACC, typename T>
-__device__ __forceinline__ void line1(const T* __restrict__ Mt, const T* s, int si, T* d, int so) {
-  T in[NI];
-#pragma unroll
-  for (int a = 0; a < NI; ++a) in[a] = s[a * si];
-#pragma unroll
-  for (int b = 0; b < NO; ++b) {
-    T acc = ACC ? d[b * so] : T(0);
-#pragma unroll
-    for (int a = 0; a < NI; ++a) acc += (TR ? Mt[a * NO + b] : Mt[b * NI + a]) * in[a];
-    d[b * so] = acc;
-  }
-}
-
 // Forward stages.  On entry X [3][n][n][XN] (in region 1) holds the element
 // coefficients; on exit U [3][Q^3] (region 0) holds values at the Gauss
 // points and, if GRAD, Gx, Gy, Gz (regions 1, 2, 3) the reference
@@ -130,8 +301,10 @@ __device__ __forceinline__ void line1(const T* __restrict__ Mt, const T* s, int 
 //   F3 z-interpolation  A2 -> U, with the z-derivative of the same column
 //      taken in registers (collocation matrix DQ)
 //   D  x- and y-derivatives of U.
+// All contractions use the even-odd half tables; `pairs` selects the nodal
+// pairing of the mode-side values.
 template <typename T, int P, bool GRAD>
-__device__ __forceinline__ void forward_stages(const ElemTables<T, P>& tb, T* sm) {
+__device__ __forceinline__ void forward_stages(const ElemTables<T, P>& tb, int pairs, T* sm) {
   using G = Geo<P>;
   constexpr int n = G::n, Q = G::Q, XQ = G::XQ, XN = G::XN, FQ = G::FQ;
   T* U = sm;
@@ -143,7 +316,11 @@ __device__ __forceinline__ void forward_stages(const ElemTables<T, P>& tb, T* sm
     constexpr int L = n * n;
     if (t < 3 * L) {
       const int c = t / L, l = t - c * L;
-      line1<n, Q, false, false>(tb.B, R1 + c * G::SX + l * XN, 1, R2 + c * G::SA1 + l * XQ, 1);
+      T in[n], out[Q];
+      load_line(R1 + c * G::SX + l * XN, 1, in);
+      if (pairs) to_canonical(in);
+      eo_interp(tb, in, out);
+      store_line(R2 + c * G::SA1 + l * XQ, 1, out);
     }
   }
   __syncthreads();
@@ -151,8 +328,11 @@ __device__ __forceinline__ void forward_stages(const ElemTables<T, P>& tb, T* sm
     constexpr int L = n * Q;
     if (t < 3 * L) {
       const int c = t / L, l = t - c * L, r = l / Q, qx = l - r * Q;
-      line1<n, Q, false, false>(tb.B, R2 + c * G::SA1 + r * n * XQ + qx, XQ, R1 + c * G::SA2 + r * Q * XQ + qx,
-                                XQ);
+      T in[n], out[Q];
+      load_line(R2 + c * G::SA1 + r * n * XQ + qx, XQ, in);
+      if (pairs) to_canonical(in);
+      eo_interp(tb, in, out);
+      store_line(R1 + c * G::SA2 + r * Q * XQ + qx, XQ, out);
     }
   }
   __syncthreads();
@@ -160,29 +340,16 @@ __device__ __forceinline__ void forward_stages(const ElemTables<T, P>& tb, T* sm
     constexpr int L = Q * Q;
     if (t < 3 * L) {
       const int c = t / L, l = t - c * L, qy = l / Q, qx = l - qy * Q;
-      const T* s = R1 + c * G::SA2 + qy * XQ + qx;
-      T in[n];
-#pragma unroll
-      for (int a = 0; a < n; ++a) in[a] = s[a * Q * XQ];
-      T u[Q];
-#pragma unroll
-      for (int b = 0; b < Q; ++b) {
-        T acc = T(0);
-#pragma unroll
-        for (int a = 0; a < n; ++a) acc += tb.B[b * n + a] * in[a];
-        u[b] = acc;
-      }
+      T in[n], u[Q];
+      load_line(R1 + c * G::SA2 + qy * XQ + qx, Q * XQ, in);
+      if (pairs) to_canonical(in);
+      eo_interp(tb, in, u);
       const int o = c * FQ + qy * XQ + qx;
-#pragma unroll
-      for (int b = 0; b < Q; ++b) U[o + b * Q * XQ] = u[b];
+      store_line(U + o, Q * XQ, u);
       if (GRAD) {
-#pragma unroll
-        for (int b = 0; b < Q; ++b) {
-          T acc = T(0);
-#pragma unroll
-          for (int m = 0; m < Q; ++m) acc += tb.DQ[b * Q + m] * u[m];
-          R3[o + b * Q * XQ] = acc;
-        }
+        T dz[Q];
+        eo_deriv(tb, u, dz);
+        store_line(R3 + o, Q * XQ, dz);
       }
     }
   }
@@ -191,10 +358,15 @@ __device__ __forceinline__ void forward_stages(const ElemTables<T, P>& tb, T* sm
     constexpr int L = Q * Q;
     if (t < 3 * L) {
       const int c = t / L, l = t - c * L, hi = l / Q, lo = l - hi * Q;
+      T v[Q], dv[Q];
       // x-lines at (qz = hi, qy = lo)
-      line1<Q, Q, false, false>(tb.DQ, U + c * FQ + l * XQ, 1, R1 + c * FQ + l * XQ, 1);
+      load_line(U + c * FQ + l * XQ, 1, v);
+      eo_deriv(tb, v, dv);
+      store_line(R1 + c * FQ + l * XQ, 1, dv);
       // y-lines at (qz = hi, qx = lo)
-      line1<Q, Q, false, false>(tb.DQ, U + c * FQ + hi * Q * XQ + lo, XQ, R2 + c * FQ + hi * Q * XQ + lo, XQ);
+      load_line(U + c * FQ + hi * Q * XQ + lo, XQ, v);
+      eo_deriv(tb, v, dv);
+      store_line(R2 + c * FQ + hi * Q * XQ + lo, XQ, dv);
     }
     __syncthreads();
   }
@@ -208,7 +380,7 @@ __device__ __forceinline__ void forward_stages(const ElemTables<T, P>& tb, T* sm
 //   T2        y: A2' -> A1' [3][n][n][Q] (region 2)
 //   T1        x: A1' -> Y (region 1)
 template <typename T, int P, bool GRAD>
-__device__ __forceinline__ void transpose_stages(const ElemTables<T, P>& tb, T* sm) {
+__device__ __forceinline__ void transpose_stages(const ElemTables<T, P>& tb, int pairs, T* sm) {
   using G = Geo<P>;
   constexpr int n = G::n, Q = G::Q, XQ = G::XQ, XN = G::XN, FQ = G::FQ;
   T* U = sm;
@@ -220,12 +392,18 @@ __device__ __forceinline__ void transpose_stages(const ElemTables<T, P>& tb, T* 
     constexpr int L = Q * Q;
     if (t < 3 * L) {  // DTx: x-lines at (c, qz, qy)
       const int c = t / L, l = t - c * L;
-      line1<Q, Q, true, true>(tb.DQ, R1 + c * FQ + l * XQ, 1, U + c * FQ + l * XQ, 1);
+      T g[Q], r[Q];
+      load_line(R1 + c * FQ + l * XQ, 1, g);
+      eo_deriv_t(tb, g, r);
+      add_line(U + c * FQ + l * XQ, 1, r);
     }
     __syncthreads();
     if (t < 3 * L) {  // DTy: y-lines at (c, qz, qx)
       const int c = t / L, l = t - c * L, qz = l / Q, qx = l - qz * Q;
-      line1<Q, Q, true, true>(tb.DQ, R2 + c * FQ + qz * Q * XQ + qx, XQ, U + c * FQ + qz * Q * XQ + qx, XQ);
+      T g[Q], r[Q];
+      load_line(R2 + c * FQ + qz * Q * XQ + qx, XQ, g);
+      eo_deriv_t(tb, g, r);
+      add_line(U + c * FQ + qz * Q * XQ + qx, XQ, r);
     }
     __syncthreads();
   }
@@ -235,28 +413,18 @@ __device__ __forceinline__ void transpose_stages(const ElemTables<T, P>& tb, T* 
       const int c = t / L, l = t - c * L, qy = l / Q, qx = l - qy * Q;
       const int o = c * FQ + qy * XQ + qx;
       T w[Q];
-#pragma unroll
-      for (int a = 0; a < Q; ++a) w[a] = U[o + a * Q * XQ];
+      load_line(U + o, Q * XQ, w);
       if (GRAD) {
-        T g[Q];
+        T g[Q], r[Q];
+        load_line(R3 + o, Q * XQ, g);
+        eo_deriv_t(tb, g, r);
 #pragma unroll
-        for (int a = 0; a < Q; ++a) g[a] = R3[o + a * Q * XQ];
-#pragma unroll
-        for (int b = 0; b < Q; ++b) {
-          T acc = w[b];
-#pragma unroll
-          for (int a = 0; a < Q; ++a) acc += tb.DQ[a * Q + b] * g[a];
-          w[b] = acc;
-        }
+        for (int a = 0; a < Q; ++a) w[a] += r[a];
       }
-      T* d = R1 + c * G::SA2 + qy * XQ + qx;
-#pragma unroll
-      for (int p = 0; p < n; ++p) {
-        T acc = T(0);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) acc += tb.B[a * n + p] * w[a];
-        d[p * Q * XQ] = acc;
-      }
+      T out[n];
+      eo_interp_t(tb, w, out);
+      if (pairs) from_canonical(out);
+      store_line(R1 + c * G::SA2 + qy * XQ + qx, Q * XQ, out);
     }
   }
   __syncthreads();
@@ -264,7 +432,11 @@ __device__ __forceinline__ void transpose_stages(const ElemTables<T, P>& tb, T* 
     constexpr int L = n * Q;
     if (t < 3 * L) {
       const int c = t / L, l = t - c * L, r = l / Q, qx = l - r * Q;
-      line1<Q, n, true, false>(tb.B, R1 + c * G::SA2 + r * Q * XQ + qx, XQ, R2 + c * G::SA1 + r * n * XQ + qx, XQ);
+      T in[Q], out[n];
+      load_line(R1 + c * G::SA2 + r * Q * XQ + qx, XQ, in);
+      eo_interp_t(tb, in, out);
+      if (pairs) from_canonical(out);
+      store_line(R2 + c * G::SA1 + r * n * XQ + qx, XQ, out);
     }
   }
   __syncthreads();
@@ -272,7 +444,11 @@ __device__ __forceinline__ void transpose_stages(const ElemTables<T, P>& tb, T* 
     constexpr int L = n * n;
     if (t < 3 * L) {
       const int c = t / L, l = t - c * L;
-      line1<Q, n, true, false>(tb.B, R2 + c * G::SA1 + l * XQ, 1, R1 + c * G::SX + l * XN, 1);
+      T in[Q], out[n];
+      load_line(R2 + c * G::SA1 + l * XQ, 1, in);
+      eo_interp_t(tb, in, out);
+      if (pairs) from_canonical(out);
+      store_line(R1 + c * G::SX + l * XN, 1, out);
     }
   }
   __syncthreads();
@@ -336,7 +512,7 @@ residual_kernel(const __grid_constant__ ElemParams<double, P> prm, const double*
     X[so] = u[g];
   }
   __syncthreads();
-  forward_stages<T, P, true>(prm.tab, sm);
+  forward_stages<T, P, true>(prm.tab, prm.pairs, sm);
   const T sc[3] = {prm.s[0], prm.s[1], prm.s[2]};
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
@@ -382,7 +558,7 @@ residual_kernel(const __grid_constant__ ElemParams<double, P> prm, const double*
     for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= mfac;
   }
   __syncthreads();
-  transpose_stages<T, P, true>(prm.tab, sm);
+  transpose_stages<T, P, true>(prm.tab, prm.pairs, sm);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
     int so;
@@ -428,7 +604,7 @@ tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restric
     X[so] = cons ? T(0) : (T)x[g];
   }
   __syncthreads();
-  forward_stages<T, P, STIFF>(prm.tab, sm);
+  forward_stages<T, P, STIFF>(prm.tab, prm.pairs, sm);
   const T sc[3] = {prm.s[0], prm.s[1], prm.s[2]};
   const T* ste = st + (int64_t)e * kStateFields * Q3;
   if constexpr (!STIFF) {
@@ -478,7 +654,7 @@ tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restric
     for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= mfac;
   }
   __syncthreads();
-  transpose_stages<T, P, STIFF>(prm.tab, sm);
+  transpose_stages<T, P, STIFF>(prm.tab, prm.pairs, sm);
   T dotT = T(0);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
@@ -529,7 +705,7 @@ mass_kernel(const __grid_constant__ ElemParams<T, P> prm, const double* __restri
     X[so] = (T)x[g];
   }
   __syncthreads();
-  forward_stages<T, P, false>(prm.tab, sm);
+  forward_stages<T, P, false>(prm.tab, prm.pairs, sm);
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
     const int so = (qz * Q + qy) * XQ + qx;
@@ -538,7 +714,7 @@ mass_kernel(const __grid_constant__ ElemParams<T, P> prm, const double* __restri
     for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= f;
   }
   __syncthreads();
-  transpose_stages<T, P, false>(prm.tab, sm);
+  transpose_stages<T, P, false>(prm.tab, prm.pairs, sm);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
     int so;
@@ -703,7 +879,7 @@ energy_kernel(const __grid_constant__ ElemParams<double, P> prm, const double* _
     X[so] = u[g];
   }
   __syncthreads();
-  forward_stages<T, P, true>(prm.tab, sm);
+  forward_stages<T, P, true>(prm.tab, prm.pairs, sm);
   const T sc[3] = {prm.s[0], prm.s[1], prm.s[2]};
   T acc = T(0);
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
@@ -764,7 +940,7 @@ body_load_kernel(const __grid_constant__ ElemParams<double, P> prm, const double
     for (int c = 0; c < 3; ++c) sm[c * FQ + so] = wdet * fe[c * Q3 + q];
   }
   __syncthreads();
-  transpose_stages<T, P, false>(prm.tab, sm);
+  transpose_stages<T, P, false>(prm.tab, prm.pairs, sm);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
     int so;

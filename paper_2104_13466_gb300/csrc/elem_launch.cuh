@@ -15,8 +15,20 @@ static ElemParams<T, P> make_params(const HostElemData& h, double b1) {
     p.tab.B[i] = (T)h.B[i];
     p.tab.D[i] = (T)h.D[i];
   }
-  for (int i = 0; i < Q * Q; ++i) p.tab.DQ[i] = (T)h.DQ[i];
   for (int i = 0; i < Q; ++i) p.tab.W[i] = (T)h.W[i];
+  using E = ElemTables<T, P>;
+  for (int i = 0; i < E::QH * E::NE; ++i) p.tab.TE[i] = (T)h.TE[i];
+  for (int i = 0; i < E::QH * E::NO; ++i) p.tab.TO[i] = (T)h.TO[i];
+  for (int i = 0; i < E::NE; ++i) p.tab.TEm[i] = (T)h.TEm[i];
+  for (int i = 0; i < E::QH * E::QH; ++i) {
+    p.tab.AH[i] = (T)h.AH[i];
+    p.tab.CH[i] = (T)h.CH[i];
+  }
+  for (int i = 0; i < E::QH; ++i) {
+    p.tab.CM[i] = (T)h.CM[i];
+    p.tab.DM[i] = (T)h.DM[i];
+  }
+  p.pairs = h.pairs;
   for (int d = 0; d < 3; ++d) {
     p.s[d] = (T)h.s[d];
     p.ne[d] = h.ne[d];

@@ -16,6 +16,9 @@ struct HostElemData {
   int P = 0;
   int nelem = 0;
   std::vector<double> B, D, DQ, W;   // Q x n, Q x n, Q x Q, Q (lattice order)
+  // even-odd half tables (eo_tables.h) and the nodal-pairing flag
+  std::vector<double> TE, TO, TEm, AH, CH, CM, DM;
+  int pairs = 0;
   double s[3] = {0, 0, 0};           // 2 / h_d
   double detJ = 0;
   double mu = 0, lam = 0, rho = 0;

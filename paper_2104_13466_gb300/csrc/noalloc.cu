@@ -12,6 +12,7 @@
 
 #include "../../include/sdme.h"
 #include "elem_kernels.cuh"
+#include "eo_tables.h"
 
 using namespace sdme;
 
@@ -87,7 +88,12 @@ sdme_status run(const sdme_mesh_desc* mesh, const sdme_material* mat, const doub
     prm.tab.D[i] = D[i];
   }
   for (int q = 0; q < Q; ++q) prm.tab.W[q] = wq[q];
-  gauss_derivative_matrix<Q>(xq, prm.tab.DQ);
+  double DQ[Q * Q];
+  gauss_derivative_matrix<Q>(xq, DQ);
+  const int sym = build_eo_tables(P, B, DQ, prm.tab.TE, prm.tab.TO, prm.tab.TEm, prm.tab.AH, prm.tab.CH, prm.tab.CM,
+                                  prm.tab.DM);
+  if (sym == kEoNone) return SDME_EUNSUPPORTED;
+  prm.pairs = sym == kEoNodalPairs ? 1 : 0;
   double h[3];
   int64_t N[3];
   for (int d = 0; d < 3; ++d) {
