@@ -163,6 +163,28 @@ sdme_status sdme_get_sizes(const sdme_ctx* ctx, int64_t* ndof, int N[3], int64_t
  */
 sdme_status sdme_internal_force(sdme_ctx* ctx, const double* u_dev, double* R_dev);
 
+/*
+ * Replaces the material constants (mu, lambda, rho) of the context; sizes,
+ * basis and buffers are kept.  Constraints as in sdme_create (mu > 0,
+ * lambda >= 0, rho >= 0), else SDME_EINVAL and the context is unchanged.
+ * Host-only, does not synchronise.
+ */
+sdme_status sdme_set_material(sdme_ctx* ctx, const sdme_material* mat);
+
+/*
+ * Vector-Jacobian product of the internal force R(u; mu, lambda) of
+ * sdme_internal_force (Sec. 3: P = mu (F - F^{-T}) + lambda ln J F^{-T}):
+ *   gu_dev   = (dR/du)^T w = K_T(u) w   (all DOFs, no Dirichlet treatment;
+ *              K_T is the symmetric consistent tangent of Sec. 3.1),
+ *   *gmu     = w . dR/dmu,   *glambda = w . dR/dlambda   (R is linear in both).
+ * u_dev, w_dev, gu_dev: float64 device vectors of ndof entries, caller-owned;
+ * gu_dev is overwritten.  gmu / glambda: host scalars, either may be NULL.
+ * Always float64 (also in a MIXED_FP32 context).  Stores the linearisation
+ * state at u.  Synchronises.  SDME_NONPOSITIVE_J if det F <= 0 at a Gauss point.
+ */
+sdme_status sdme_internal_force_vjp(sdme_ctx* ctx, const double* u_dev, const double* w_dev, double* gu_dev,
+                                    double* gmu, double* glambda);
+
 /* y_dev = M x_dev, consistent mass of eq. material virtual work (first term), no Dirichlet treatment. */
 sdme_status sdme_mass_apply(sdme_ctx* ctx, const double* x_dev, double* y_dev);
 
@@ -236,6 +258,49 @@ sdme_status sdme_explicit_start(sdme_ctx* ctx, sdme_explicit_state* state, doubl
  */
 sdme_status sdme_explicit_step(sdme_ctx* ctx, sdme_explicit_state* state, double dt, const double* Pn_dev,
                                double rtol, int maxit, int* pcg_iters);
+
+/*
+ * Differentiating an explicit trajectory (the central-difference scheme of
+ * Sec. 4.1, as in sdme_explicit_start / sdme_explicit_step) with respect to
+ * the material constants (mu, lambda), the initial state and the load.
+ *
+ * A tape holds checkpoints (u_n, u_{n-1}) every `every` steps, a segment
+ * buffer of `every` vectors for recomputation, and work vectors: about
+ * (2 ceil(nsteps/every) + every + 10) float64 vectors of ndof entries,
+ * owned by the tape.  It is bound to one context (used on its stream).
+ */
+typedef struct sdme_tape sdme_tape;
+
+sdme_status sdme_tape_create(sdme_ctx* ctx, int nsteps, int every, sdme_tape** out);
+sdme_status sdme_tape_destroy(sdme_tape* tape);
+
+/*
+ * Forward run recorded on the tape: start-up from (u0, v0) with P_0, then
+ * nsteps explicit steps n = 0 .. nsteps-1 with loads P_n = s_host[n] * f_dev
+ * (f_dev NULL: no load; s_host then unused, else nsteps host doubles).
+ * Every mass solve is Jacobi-PCG to rtol (maxit iterations at most).
+ * Writes u_N (N = nsteps) to uN_dev.  u0_dev, v0_dev, f_dev, uN_dev: float64
+ * device vectors of ndof entries, caller-owned (f is copied into the tape).
+ * Synchronises.
+ */
+sdme_status sdme_explicit_forward(sdme_ctx* ctx, sdme_tape* tape, double dt, const double* u0_dev,
+                                  const double* v0_dev, const double* f_dev, const double* s_host, double rtol,
+                                  int maxit, double* uN_dev);
+
+/*
+ * Discrete adjoint of the last sdme_explicit_forward on the tape for an
+ * objective J(u_N), given gN_dev = dJ/du_N.  With A the mass inverse on the
+ * free DOFs and z_n = A g_{n+1}, the sweep runs n = N-1 .. 0:
+ *   g_n = [2 g_{n+1} - g_{n+2} on free DOFs | g_{n+1} on constrained] - dt^2 K_T(u_n) z_n,
+ *   dJ/d(mu, lambda) -= dt^2 z_n . dR(u_n)/d(mu, lambda),  dJ/df += dt^2 s_n z_n,
+ * then the start-up adjoint (g_{-1} = -g_1 on free DOFs, weight dt^2 / 2).
+ * Segments between checkpoints are recomputed forward once each.  Outputs,
+ * each optional (NULL): gmu, glambda (host doubles), gu0_dev, gv0_dev, gf_dev
+ * (float64 device vectors, overwritten).  The context's material must be the
+ * one of the forward run.  Synchronises.
+ */
+sdme_status sdme_explicit_adjoint(sdme_ctx* ctx, sdme_tape* tape, const double* gN_dev, double* gmu,
+                                  double* glambda, double* gu0_dev, double* gv0_dev, double* gf_dev);
 
 /*
  * Kinetic energy 1/2 v^T M v and strain energy int Psi(F(u)) dV (eq.

@@ -25,6 +25,8 @@ numpy at float64 from Dias, Suzuki, Valente, Bittencourt (arXiv:2104.13466):
 * ``solvers``      Jacobi-PCG, dense direct solve, Newton-Newmark step
                    (Sec. 4.2, eqs. newmark_acceleration, NR_explicit).
 * ``manufactured`` fabricated-solution body forces and tractions (Sec. 5).
+* ``adjoint``      vector-Jacobian product of the internal force and the
+                   discrete adjoint of the explicit scheme (Sec. 4.1).
 
 Every function whose result is not pinned to something outside itself says
 "parity unpinned" in its docstring; the tests in ``tests/test_oracle_*.py``

@@ -31,7 +31,9 @@ EXPORTS = ("sdme_status_string", "sdme_build_basis1d", "sdme_create", "sdme_dest
            "sdme_internal_force", "sdme_mass_apply", "sdme_tangent_apply", "sdme_diagonal", "sdme_pcg_solve",
            "sdme_traction_load", "sdme_implicit_newmark_step", "sdme_set_timing", "sdme_get_timing",
            "sdme_tangent_apply_noalloc", "sdme_cuda_error_string", "sdme_explicit_start", "sdme_explicit_step",
-           "sdme_energy", "sdme_estimate_dt_crit", "sdme_body_load", "sdme_mass_solve", "sdme_gauss_points")
+           "sdme_energy", "sdme_estimate_dt_crit", "sdme_body_load", "sdme_mass_solve", "sdme_gauss_points",
+           "sdme_set_material", "sdme_internal_force_vjp", "sdme_tape_create", "sdme_tape_destroy",
+           "sdme_explicit_forward", "sdme_explicit_adjoint")
 
 
 class BasisDesc(ctypes.Structure):
@@ -106,6 +108,12 @@ def _load():
     lib.sdme_body_load.argtypes = [vp, vp, vp]
     lib.sdme_mass_solve.argtypes = [vp, vp, vp, d, i, ctypes.POINTER(i), pd]
     lib.sdme_gauss_points.argtypes = [vp, pd, pd]
+    lib.sdme_set_material.argtypes = [vp, ctypes.POINTER(Material)]
+    lib.sdme_internal_force_vjp.argtypes = [vp, vp, vp, vp, pd, pd]
+    lib.sdme_tape_create.argtypes = [vp, i, i, ctypes.POINTER(vp)]
+    lib.sdme_tape_destroy.argtypes = [vp]
+    lib.sdme_explicit_forward.argtypes = [vp, vp, d, vp, vp, vp, pd, d, i, vp]
+    lib.sdme_explicit_adjoint.argtypes = [vp, vp, vp, pd, pd, vp, vp, vp]
     lib.sdme_set_timing.argtypes = [vp, i]
     lib.sdme_get_timing.argtypes = [vp, ctypes.POINTER(Timing)]
     lib.sdme_tangent_apply_noalloc.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(Material), i, pd, pd, pd,
@@ -248,6 +256,22 @@ class Context:
     def internal_force(self, u, R):
         return _check(lib.sdme_internal_force(self._h, _ptr(u), _ptr(R)), "sdme_internal_force", ctx=self._h)
 
+    def set_material(self, mu, lam, rho=None):
+        m = Material(float(mu), float(lam), float(self._mat.rho if rho is None else rho))
+        _check(lib.sdme_set_material(self._h, ctypes.byref(m)), "sdme_set_material")
+        self._mat = m
+
+    @property
+    def material(self):
+        return self._mat.mu, self._mat.lam, self._mat.rho
+
+    def internal_force_vjp(self, u, w, gu):
+        """gu = (dR/du)^T w (overwritten); returns (w . dR/dmu, w . dR/dlambda)."""
+        gmu, glam = ctypes.c_double(), ctypes.c_double()
+        _check(lib.sdme_internal_force_vjp(self._h, _ptr(u), _ptr(w), _ptr(gu), ctypes.byref(gmu),
+                                           ctypes.byref(glam)), "sdme_internal_force_vjp", ctx=self._h)
+        return gmu.value, glam.value
+
     def mass_apply(self, x, y):
         return _check(lib.sdme_mass_apply(self._h, _ptr(x), _ptr(y)), "sdme_mass_apply", ctx=self._h)
 
@@ -362,3 +386,143 @@ class Context:
         _check(lib.sdme_get_timing(self._h, ctypes.byref(t)), "sdme_get_timing")
         return {"tangent_ms": t.tangent_ms, "tangent_launches": t.tangent_launches,
                 "kernel_launches": t.kernel_launches}
+
+
+def _material_grad(x, g):
+    """Gradient g (a float) in the type of the material input x."""
+    import torch
+    if isinstance(x, torch.Tensor) and x.requires_grad:
+        return torch.tensor(g, dtype=x.dtype, device=x.device).reshape(x.shape)
+    return None
+
+
+def _InternalForceFunction():
+    import torch
+
+    class InternalForce(torch.autograd.Function):
+        """R(u; mu, lambda) of sdme_internal_force with the hand-written
+        adjoint of sdme_internal_force_vjp as its backward."""
+
+        @staticmethod
+        def forward(fctx, ctx, u, mu, lam):
+            ctx.set_material(float(mu), float(lam))
+            R = torch.empty_like(u)
+            ctx.internal_force(u, R)
+            fctx.sdme = ctx
+            fctx.mat = (float(mu), float(lam))
+            fctx.mu_in, fctx.lam_in = mu, lam
+            fctx.save_for_backward(u)
+            return R
+
+        @staticmethod
+        def backward(fctx, gR):
+            (u,) = fctx.saved_tensors
+            ctx = fctx.sdme
+            ctx.set_material(*fctx.mat)
+            gu = torch.empty_like(u)
+            gmu, glam = ctx.internal_force_vjp(u, gR.contiguous(), gu)
+            return None, gu, _material_grad(fctx.mu_in, gmu), _material_grad(fctx.lam_in, glam)
+
+    return InternalForce
+
+
+_internal_force_fn = None
+
+
+def internal_force(ctx, u, mu, lam):
+    """Differentiable internal force R(u; mu, lambda) (float64 CUDA u; mu and
+    lam floats or 0-dim tensors).  Sets the context's material to (mu, lam)."""
+    global _internal_force_fn
+    if _internal_force_fn is None:
+        _internal_force_fn = _InternalForceFunction()
+    return _internal_force_fn.apply(ctx, u, mu, lam)
+
+
+class Tape:
+    """Owns an sdme_tape: a checkpointed explicit trajectory of ``ctx``
+    (``nsteps`` steps, checkpoints every ``every`` steps) and its adjoint."""
+
+    def __init__(self, ctx, nsteps, every):
+        h = ctypes.c_void_p()
+        _check(lib.sdme_tape_create(ctx._h, int(nsteps), int(every), ctypes.byref(h)), "sdme_tape_create",
+               ctx=ctx._h)
+        self._h, self.ctx, self.nsteps, self.every = h, ctx, int(nsteps), int(every)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.sdme_tape_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, dt, u0, v0, uN, f=None, s=None, rtol=1e-12, maxit=20000):
+        """Runs the trajectory; writes u_N into uN.  Loads P_n = s[n] f."""
+        import numpy as np
+        sp = None
+        if f is not None:
+            s = np.ascontiguousarray(np.broadcast_to(np.asarray(1.0 if s is None else s, dtype=np.float64),
+                                                     (self.nsteps,)))
+            self._s = s
+            sp = s.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(lib.sdme_explicit_forward(self.ctx._h, self._h, float(dt), _ptr(u0), _ptr(v0),
+                                         _ptr(f) if f is not None else None, sp, float(rtol), int(maxit),
+                                         _ptr(uN)), "sdme_explicit_forward", ctx=self.ctx._h)
+
+    def adjoint(self, gN, gu0=None, gv0=None, gf=None):
+        """Reverse sweep for dJ/du_N = gN; fills the given device vectors and
+        returns (dJ/dmu, dJ/dlambda)."""
+        gmu, glam = ctypes.c_double(), ctypes.c_double()
+        opt = [_ptr(t) if t is not None else None for t in (gu0, gv0, gf)]
+        _check(lib.sdme_explicit_adjoint(self.ctx._h, self._h, _ptr(gN), ctypes.byref(gmu), ctypes.byref(glam),
+                                         *opt), "sdme_explicit_adjoint", ctx=self.ctx._h)
+        return gmu.value, glam.value
+
+
+def _TrajectoryFunction():
+    import torch
+
+    class ExplicitTrajectory(torch.autograd.Function):
+        """u_N of a checkpointed explicit trajectory as a function of
+        (u0, v0, f, mu, lambda); backward is the hand-written discrete adjoint."""
+
+        @staticmethod
+        def forward(fctx, tape, dt, s, rtol, u0, v0, f, mu, lam):
+            ctx = tape.ctx
+            ctx.set_material(float(mu), float(lam))
+            uN = torch.empty_like(u0)
+            tape.forward(dt, u0, v0, uN, f=f, s=s, rtol=rtol)
+            fctx.tape, fctx.mat = tape, (float(mu), float(lam))
+            fctx.mu_in, fctx.lam_in, fctx.has_f = mu, lam, f is not None
+            return uN
+
+        @staticmethod
+        def backward(fctx, gN):
+            tape = fctx.tape
+            tape.ctx.set_material(*fctx.mat)
+            need = fctx.needs_input_grad
+            gu0 = torch.empty_like(gN) if need[4] else None
+            gv0 = torch.empty_like(gN) if need[5] else None
+            gf = torch.empty_like(gN) if (need[6] and fctx.has_f) else None
+            gmu, glam = tape.adjoint(gN.contiguous(), gu0, gv0, gf)
+            return (None, None, None, None, gu0, gv0, gf, _material_grad(fctx.mu_in, gmu),
+                    _material_grad(fctx.lam_in, glam))
+
+    return ExplicitTrajectory
+
+
+_trajectory_fn = None
+
+
+def explicit_trajectory(tape, dt, u0, v0, mu, lam, f=None, s=None, rtol=1e-12):
+    """Differentiable u_N of the explicit scheme (start-up from (u0, v0),
+    tape.nsteps steps, loads s[n] f).  Backward runs the discrete adjoint on
+    the tape; the tape holds one trajectory, so call backward before the
+    next forward on the same tape."""
+    global _trajectory_fn
+    if _trajectory_fn is None:
+        _trajectory_fn = _TrajectoryFunction()
+    return _trajectory_fn.apply(tape, dt, s, rtol, u0, v0, f, mu, lam)

@@ -359,6 +359,67 @@ void free_all(sdme_ctx* ctx) {
 
 }  // namespace
 
+//-----------------------------------------------------------------------------
+// Checkpointed explicit trajectory and its discrete adjoint.
+//-----------------------------------------------------------------------------
+struct sdme_tape {
+  sdme_ctx* ctx = nullptr;
+  int nsteps = 0, every = 0, nck = 0;
+  double dt = 0.0, rtol = 0.0;
+  int maxit = 0;
+  bool have_f = false, ran = false;
+  std::vector<double> s;     // load schedule, P_n = s[n] f
+  double* f = nullptr;       // load shape (ndof)
+  double* ck = nullptr;      // nck x 2 x ndof: (u_n, u_{n-1}) at n = k * every
+  double* seg = nullptr;     // every x ndof: u_{n0} .. u_{n0 + every - 1} of the segment being reversed
+  double* v[9] = {};         // u, u_prev, a, P_n, g_{n+2}, g_{n+1}, z, K z, adjoint right-hand side
+};
+
+namespace {
+
+// P_n = s[n] f into the tape's load vector (zero without a load shape)
+sdme_status tape_load(sdme_tape* tp, int n) {
+  sdme_ctx* ctx = tp->ctx;
+  if (tp->have_f) {
+    k_to_double<double><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, tp->f, tp->s[n], tp->v[3]);
+    SDME_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 1;
+  } else {
+    SDME_CUDA(cudaMemsetAsync(tp->v[3], 0, sizeof(double) * ctx->ndof, ctx->stream));
+  }
+  return SDME_OK;
+}
+
+sdme_status copy_vec(sdme_ctx* ctx, double* dst, const double* src) {
+  SDME_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * ctx->ndof, cudaMemcpyDeviceToDevice, ctx->stream));
+  return SDME_OK;
+}
+
+// z = A g (mass solve on the free DOFs), then K_T(u) z and the material
+// partials; accumulates -c (w . dR/dmu, w . dR/dlambda) into gth and
+// c s_n z into gf.
+sdme_status adjoint_kernel_step(sdme_tape* tp, const double* u, const double* g, double c, double sn, double* gth,
+                                double* gf) {
+  sdme_ctx* ctx = tp->ctx;
+  double* z = tp->v[6];
+  double* Kz = tp->v[7];
+  int its = 0;
+  double rel = 0.0;
+  SDME_TRY(pcg_dispatch(ctx, 1.0, g, z, tp->rtol, tp->maxit, &its, &rel, true));
+  double pm = 0.0, pl = 0.0;
+  SDME_TRY(sdme_internal_force_vjp(ctx, u, z, Kz, &pm, &pl));
+  gth[0] -= c * pm;
+  gth[1] -= c * pl;
+  if (gf) {
+    k_axpy<double><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, c * sn, z, gf);
+    SDME_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 1;
+  }
+  return SDME_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* sdme_status_string(sdme_status s) {
@@ -480,7 +541,7 @@ sdme_status sdme_create(sdme_ctx** out, const sdme_mesh_desc* mesh, const sdme_m
   ctx->own_stream = false;
   const int64_t nst = nelem * kStateFields * (int64_t)Q * Q * Q;
   const int64_t nd = ctx->ndof;
-  const int64_t npart = std::max<int64_t>(nelem, 2 * kVecBlocks) + 64;
+  const int64_t npart = std::max<int64_t>(2 * nelem, 2 * kVecBlocks) + 64;
   bool ok = true;
   ok = ok && dalloc(&ctx->st64, nst) == cudaSuccess;
   if (prec == SDME_MIXED_FP32) ok = ok && dalloc(&ctx->st32, nst) == cudaSuccess;
@@ -548,6 +609,39 @@ sdme_status sdme_internal_force(sdme_ctx* ctx, const double* u_dev, double* R_de
   if (!ctx || !u_dev || !R_dev) return SDME_EINVAL;
   SDME_TRY(residual_launch(ctx, 0.0, u_dev, R_dev));
   return sync_and_check(ctx);
+}
+
+sdme_status sdme_set_material(sdme_ctx* ctx, const sdme_material* mat) {
+  if (!ctx || !mat) return SDME_EINVAL;
+  if (!(mat->mu > 0.0) || !(mat->lambda >= 0.0) || !(mat->rho >= 0.0)) return SDME_EINVAL;
+  ctx->mat = *mat;
+  ctx->h.mu = mat->mu;
+  ctx->h.lam = mat->lambda;
+  ctx->h.rho = mat->rho;
+  // the captured PCG chunk holds the old parameter blocks
+  for (cudaGraphExec_t& g : ctx->gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  return SDME_OK;
+}
+
+sdme_status sdme_internal_force_vjp(sdme_ctx* ctx, const double* u_dev, const double* w_dev, double* gu_dev,
+                                    double* gmu, double* glambda) {
+  if (!ctx || !u_dev || !w_dev || !gu_dev) return SDME_EINVAL;
+  SDME_TRY(residual_launch(ctx, 0.0, u_dev, ctx->y));
+  SDME_CUDA(cudaMemsetAsync(gu_dev, 0, sizeof(double) * ctx->ndof, ctx->stream));
+  SDME_CUDA(dispatch_P(ctx->h.P, [&](auto Pc) {
+    return launch_vjp<decltype(Pc)::value>(ctx->h, w_dev, gu_dev, ctx->st64, ctx->partial, ctx->dcount,
+                                           ctx->dscal, ctx->stream);
+  }));
+  ctx->kernel_launches += 1;
+  SDME_CUDA(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  SDME_TRY(sync_and_check(ctx));
+  if (gmu) *gmu = ctx->dscal_h[0];
+  if (glambda) *glambda = ctx->dscal_h[1];
+  return SDME_OK;
 }
 
 sdme_status sdme_mass_apply(sdme_ctx* ctx, const double* x_dev, double* y_dev) {
@@ -833,6 +927,126 @@ sdme_status sdme_get_timing(sdme_ctx* ctx, sdme_timing* out) {
   out->tangent_ms = ctx->tangent_ms;
   out->tangent_launches = ctx->tangent_launches;
   out->kernel_launches = ctx->kernel_launches;
+  return SDME_OK;
+}
+
+sdme_status sdme_tape_create(sdme_ctx* ctx, int nsteps, int every, sdme_tape** out) {
+  if (!ctx || !out || nsteps < 1 || every < 1) return SDME_EINVAL;
+  *out = nullptr;
+  sdme_tape* tp = new (std::nothrow) sdme_tape();
+  if (!tp) return SDME_ENOMEM;
+  tp->ctx = ctx;
+  tp->nsteps = nsteps;
+  tp->every = std::min(every, nsteps);
+  tp->nck = (nsteps + tp->every - 1) / tp->every;
+  const size_t nd = (size_t)ctx->ndof;
+  bool ok = dalloc(&tp->f, nd) == cudaSuccess && dalloc(&tp->ck, 2 * nd * tp->nck) == cudaSuccess &&
+            dalloc(&tp->seg, nd * tp->every) == cudaSuccess;
+  for (double*& p : tp->v) ok = ok && dalloc(&p, nd) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    sdme_tape_destroy(tp);
+    return SDME_ENOMEM;
+  }
+  *out = tp;
+  return SDME_OK;
+}
+
+sdme_status sdme_tape_destroy(sdme_tape* tp) {
+  if (!tp) return SDME_OK;
+  if (tp->ctx) cudaStreamSynchronize(tp->ctx->stream);
+  for (double* p : {tp->f, tp->ck, tp->seg}) if (p) cudaFree(p);
+  for (double* p : tp->v)
+    if (p) cudaFree(p);
+  delete tp;
+  return SDME_OK;
+}
+
+
+sdme_status sdme_explicit_forward(sdme_ctx* ctx, sdme_tape* tp, double dt, const double* u0_dev, const double* v0_dev,
+                                  const double* f_dev, const double* s_host, double rtol, int maxit, double* uN_dev) {
+  if (!ctx || !tp || tp->ctx != ctx || !u0_dev || !v0_dev || !uN_dev || !(dt > 0.0) || maxit < 1 ||
+      !(rtol >= 0.0) || (f_dev && !s_host))
+    return SDME_EINVAL;
+  tp->ran = false;
+  tp->dt = dt;
+  tp->rtol = rtol;
+  tp->maxit = maxit;
+  tp->have_f = f_dev != nullptr;
+  tp->s.assign(tp->nsteps, 0.0);
+  if (f_dev) {
+    for (int n = 0; n < tp->nsteps; ++n) tp->s[n] = s_host[n];
+    SDME_TRY(copy_vec(ctx, tp->f, f_dev));
+  }
+  const size_t nd = (size_t)ctx->ndof;
+  sdme_explicit_state st{tp->v[0], tp->v[1], tp->v[2]};
+  SDME_TRY(copy_vec(ctx, st.u, u0_dev));
+  SDME_TRY(tape_load(tp, 0));
+  SDME_TRY(sdme_explicit_start(ctx, &st, dt, tp->v[3], v0_dev, rtol, maxit));
+  for (int n = 0; n < tp->nsteps; ++n) {
+    if (n % tp->every == 0) {
+      double* c = tp->ck + 2 * nd * (n / tp->every);
+      SDME_TRY(copy_vec(ctx, c, st.u));
+      SDME_TRY(copy_vec(ctx, c + nd, st.u_prev));
+    }
+    SDME_TRY(tape_load(tp, n));
+    SDME_TRY(sdme_explicit_step(ctx, &st, dt, tp->v[3], rtol, maxit, nullptr));
+  }
+  SDME_TRY(copy_vec(ctx, uN_dev, st.u));
+  SDME_CUDA(cudaStreamSynchronize(ctx->stream));
+  tp->ran = true;
+  return SDME_OK;
+}
+
+sdme_status sdme_explicit_adjoint(sdme_ctx* ctx, sdme_tape* tp, const double* gN_dev, double* gmu, double* glambda,
+                                  double* gu0_dev, double* gv0_dev, double* gf_dev) {
+  if (!ctx || !tp || tp->ctx != ctx || !gN_dev || !tp->ran) return SDME_EINVAL;
+  const size_t nd = (size_t)ctx->ndof;
+  const int N = tp->nsteps;
+  const double dt = tp->dt, dt2 = dt * dt;
+  double* g2 = tp->v[4];  // g_{n+2}
+  double* g1 = tp->v[5];  // g_{n+1}
+  SDME_CUDA(cudaMemsetAsync(g2, 0, sizeof(double) * nd, ctx->stream));
+  SDME_TRY(copy_vec(ctx, g1, gN_dev));
+  if (gf_dev) SDME_CUDA(cudaMemsetAsync(gf_dev, 0, sizeof(double) * nd, ctx->stream));
+  double gth[2] = {0.0, 0.0};
+  for (int k = tp->nck - 1; k >= 0; --k) {
+    const int n0 = k * tp->every, n1 = std::min(n0 + tp->every, N);
+    // recompute u_{n0} .. u_{n1-1} from the checkpoint (u_{n0}, u_{n0-1})
+    sdme_explicit_state st{tp->v[0], tp->v[1], tp->v[2]};
+    const double* c = tp->ck + 2 * nd * k;
+    SDME_TRY(copy_vec(ctx, st.u, c));
+    SDME_TRY(copy_vec(ctx, st.u_prev, c + nd));
+    SDME_TRY(copy_vec(ctx, tp->seg, c));
+    for (int n = n0; n < n1 - 1; ++n) {
+      SDME_TRY(tape_load(tp, n));
+      SDME_TRY(sdme_explicit_step(ctx, &st, dt, tp->v[3], tp->rtol, tp->maxit, nullptr));
+      SDME_TRY(copy_vec(ctx, tp->seg + nd * (n + 1 - n0), st.u));
+    }
+    // reverse sweep over the segment: g_n from g_{n+1}, g_{n+2}
+    for (int n = n1 - 1; n >= n0; --n) {
+      SDME_TRY(adjoint_kernel_step(tp, tp->seg + nd * (n - n0), g1, dt2, tp->s[n], gth, gf_dev));
+      k_adj_step<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, g1, g2, tp->v[7], dt2, g2);
+      SDME_CUDA(cudaGetLastError());
+      ctx->kernel_launches += 1;
+      std::swap(g1, g2);  // g1 <- g_n, g2 <- g_{n+1}
+    }
+  }
+  // start-up: g1 = g_0, g2 = g_1; rhs = g_{-1} = -g_1 on free DOFs
+  double* rhs = tp->v[8];
+  k_masked_scale<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, g2, -1.0, rhs);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 1;
+  SDME_TRY(adjoint_kernel_step(tp, tp->ck, rhs, 0.5 * dt2, tp->s[0], gth, gf_dev));
+  if (gu0_dev || gv0_dev) {
+    k_adj_start<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, g1, g2, tp->v[7], 0.5 * dt2, dt, gu0_dev,
+                                                             gv0_dev);
+    SDME_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 1;
+  }
+  SDME_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (gmu) *gmu = gth[0];
+  if (glambda) *glambda = gth[1];
   return SDME_OK;
 }
 

@@ -46,6 +46,9 @@ cudaError_t launch_mass_diag(const HostElemData& h, double b1, T* y, cudaStream_
 template <int P>
 cudaError_t launch_body_load(const HostElemData& h, const double* fq, double* y, cudaStream_t s);
 template <int P>
+cudaError_t launch_vjp(const HostElemData& h, const double* w, double* gu, const double* st, double* partial,
+                       unsigned int* counter, double* out, cudaStream_t s);
+template <int P>
 cudaError_t launch_energy(const HostElemData& h, const double* u, double* partial, unsigned int* counter,
                           double* out, int* err, cudaStream_t s);
 

@@ -1,6 +1,7 @@
 // Element kernels instantiated for polynomial order P = 6.
-#include "elem_launch.cuh"
+#include "elem_adjoint.cuh"
 
 namespace sdme {
 SDME_INSTANTIATE_ORDER(6)
+SDME_INSTANTIATE_ADJOINT(6)
 }  // namespace sdme

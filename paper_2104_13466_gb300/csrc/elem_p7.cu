@@ -1,6 +1,7 @@
 // Element kernels instantiated for polynomial order P = 7.
-#include "elem_launch.cuh"
+#include "elem_adjoint.cuh"
 
 namespace sdme {
 SDME_INSTANTIATE_ORDER(7)
+SDME_INSTANTIATE_ADJOINT(7)
 }  // namespace sdme

@@ -1,6 +1,7 @@
 // Element kernels instantiated for polynomial order P = 8.
-#include "elem_launch.cuh"
+#include "elem_adjoint.cuh"
 
 namespace sdme {
 SDME_INSTANTIATE_ORDER(8)
+SDME_INSTANTIATE_ADJOINT(8)
 }  // namespace sdme

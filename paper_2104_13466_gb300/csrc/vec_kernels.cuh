@@ -341,4 +341,43 @@ __global__ void __launch_bounds__(kVecThreads) k_scale(int64_t n, double s, doub
     x[g] *= s;
 }
 
+
+// Discrete adjoint of one central-difference step.  The step maps
+// (u_n, u_{n-1}) to u_{n+1} = 2 u_n - u_{n-1} + dt^2 A (P_n - R(u_n)) on free
+// DOFs and u_n on constrained ones (A: mass inverse on the free DOFs), so
+// g_n = dJ/du_n = [2 g_{n+1} - g_{n+2} | g_{n+1}] - dt^2 K_T(u_n) z_n with
+// z_n = A g_{n+1}.  out may alias g2 (element-wise in place).
+__global__ void __launch_bounds__(kVecThreads) k_adj_step(MeshInfo mi, const double* g1, const double* g2,
+                                                          const double* __restrict__ Kz, double dt2, double* out) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const double a = g1[g];
+    const double b = dof_constrained(mi, g) ? a : 2.0 * a - g2[g];
+    out[g] = b - dt2 * Kz[g];
+  }
+}
+
+// out = a x on free DOFs, 0 on constrained ones.
+__global__ void __launch_bounds__(kVecThreads) k_masked_scale(MeshInfo mi, const double* __restrict__ x, double a,
+                                                              double* __restrict__ out) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
+       g += (int64_t)gridDim.x * blockDim.x)
+    out[g] = dof_constrained(mi, g) ? 0.0 : a * x[g];
+}
+
+// Adjoint of the start-up u_{-1} = u_0 - dt v_0 + dt^2/2 A (P_0 - R(u_0)) (free
+// DOFs): with g_{-1} = -g_1 on free DOFs and z = A g_{-1},
+// dJ/du_0 = g_0 + g_{-1} - dt^2/2 K_T(u_0) z and dJ/dv_0 = -dt g_{-1}.
+__global__ void __launch_bounds__(kVecThreads) k_adj_start(MeshInfo mi, const double* __restrict__ g0,
+                                                           const double* __restrict__ g1,
+                                                           const double* __restrict__ Kz, double half_dt2, double dt,
+                                                           double* __restrict__ gu0, double* __restrict__ gv0) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const double gm1 = dof_constrained(mi, g) ? 0.0 : -g1[g];
+    if (gu0) gu0[g] = g0[g] + gm1 - half_dt2 * Kz[g];
+    if (gv0) gv0[g] = -dt * gm1;
+  }
+}
+
 }  // namespace sdme
