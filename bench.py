@@ -482,6 +482,72 @@ def run_explicit(args, w):
     print(json.dumps(out), flush=True)
 
 
+def run_adjoint(args, w):
+    """Differentiated explicit run (config 5 shape): u_N of a checkpointed
+    central-difference trajectory under a constant dead tip traction, the
+    objective J = |u_N - target|^2 over the tip face, and dJ/d(mu, lambda) by
+    the hand-written discrete adjoint; compared with central finite
+    differences (h = fd_rel_h relative) of the same GPU forward run."""
+    import torch
+    import paper_2104_13466_gb300 as sd
+    from synthetic import random_uniform
+    mu, lam = lame(w["E"], w["nu"])
+    ctx = sd.Context(w["elems"], w["lengths"], w["clamp"], mu, lam, w["rho"], w["P"], args.basis)
+    n = ctx.ndof
+    Nx, Ny, Nz = ctx.N
+    zero = torch.zeros(n, dtype=torch.float64, device="cuda")
+    f = torch.zeros_like(zero)
+    ctx.traction_load(w["traction_face"], w["traction"], f)
+    dt_crit, _ = ctx.estimate_dt_crit(zero, iters=args.dt_iters)
+    dt = w["cfl"] * dt_crit
+    # tip-face DOF indices (x = Nx - 1) and the seeded target
+    j, k = np.meshgrid(np.arange(Ny), np.arange(Nz), indexing="xy")
+    node = ((k * Ny + j) * Nx + (Nx - 1)).ravel()
+    idx = np.concatenate([c * Nx * Ny * Nz + node for c in range(3)])
+    xi = random_uniform(node.size, w["seed"])
+    target = np.zeros(idx.size)
+    target[2 * node.size:] = -w["tip_delta"] * (1.0 + 0.1 * xi)
+    idx_t = torch.from_numpy(idx).cuda()
+    tgt = torch.from_numpy(target).cuda()
+    steps, every, rtol = w["steps"], w["every"], w["mass_rtol"]
+    tape = sd.Tape(ctx, steps, every)
+    uN = torch.zeros_like(zero)
+
+    def objective(mu_, lam_):
+        ctx.set_material(mu_, lam_)
+        tape.forward(dt, zero, zero, uN, f=f, rtol=rtol)
+        return float(((uN[idx_t] - tgt) ** 2).sum())
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    objective(mu, lam)  # warm-up (kernel attributes, graph capture)
+    launches0 = ctx.timing()["kernel_launches"]
+    J, t_fwd = timed(lambda: objective(mu, lam))
+    gN = torch.zeros_like(zero)
+    gN[idx_t] = 2.0 * (uN[idx_t] - tgt)
+    (gmu, glam), t_adj = timed(lambda: tape.adjoint(gN))
+    launches = ctx.timing()["kernel_launches"] - launches0
+    h_mu, h_lam = w["fd_rel_h"] * mu, w["fd_rel_h"] * lam
+    fd_mu = (objective(mu + h_mu, lam) - objective(mu - h_mu, lam)) / (2 * h_mu)
+    fd_lam = (objective(mu, lam + h_lam) - objective(mu, lam - h_lam)) / (2 * h_lam)
+    out = {"mode": "adjoint", "workload": args.workload, "basis": args.basis, "ndof": n, "steps": steps,
+           "checkpoint_every": every, "dt": dt, "dt_crit": dt_crit, "J": J,
+           "forward_ms": t_fwd, "adjoint_ms": t_adj, "adjoint_over_forward": t_adj / t_fwd,
+           "dJ_dmu": gmu, "dJ_dlambda": glam, "fd_dmu": fd_mu, "fd_dlambda": fd_lam,
+           "rel_err_mu": abs(gmu - fd_mu) / abs(fd_mu), "rel_err_lambda": abs(glam - fd_lam) / abs(fd_lam),
+           "gpu_launches_fwd_plus_adj": launches, "fd_rel_h": w["fd_rel_h"], "mass_rtol": rtol}
+    tape.close()
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -506,9 +572,14 @@ def main():
     ap.add_argument("--bases", default="nodal,modal,sdme_m,sdme_h")
     ap.add_argument("--precisions", default="mixed,fp64")
     ap.add_argument("--kernel-iters", type=int, default=20)
+    ap.add_argument("--adjoint", action="store_true")
     args = ap.parse_args()
+    if args.adjoint and args.workload == "beam_p8":
+        args.workload = "beam_p6_adjoint"
     w = workload(args.workload)
-    if args.kernel_only:
+    if args.adjoint:
+        run_adjoint(args, w)
+    elif args.kernel_only:
         run_kernel_only(args, w)
     elif args.compare:
         run_compare(args, w)

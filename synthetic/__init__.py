@@ -19,6 +19,11 @@ lambda = 100) scaled to the GPU problem sizes:
 * ``cube_p6_explicit``  explicit central-difference run on the unit cube,
                 16^3 hexes, P = 6 (2.74 M DOFs), all faces clamped, seeded
                 sinusoidal initial velocity, 2000 steps at half the stable step.
+* ``beam_p6_adjoint``  differentiated explicit run: [0,8]x[0,1]x[0,1]
+                cantilever, 32x4x4 hexes, P = 6 (361,875 DOFs), x = 0 clamped,
+                constant dead traction on x = 8, 200 steps at half the stable
+                step, checkpoints every 20 steps; objective = squared distance of
+                the final tip-face displacement to a seeded target.
 * ``static_fab``  the paper's static fabricated problem (Sec. 5.1): unit cube,
                 2x2x2 hexes, x = 0 clamped.
 
@@ -61,6 +66,12 @@ WORKLOADS = {
         elems=(16, 16, 16), P=6, lengths=(1.0, 1.0, 1.0), E=1.0e3, nu=0.3, rho=1.0,
         clamp={f: (0, 1, 2) for f in ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")},
         v_amp=0.05, seed=0, cfl=0.5, steps=2000, mass_rtol=1e-12, mass_rtol_mixed=1e-6),
+    # objective target: tip-face lattice points, z-component
+    # -tip_delta (1 + 0.1 xi), xi ~ U(-1, 1) from `seed`, x and y components 0
+    "beam_p6_adjoint": dict(
+        elems=(32, 4, 4), P=6, lengths=(8.0, 1.0, 1.0), E=1.0e3, nu=0.3, rho=1.0,
+        clamp={"xmin": (0, 1, 2)}, traction_face="xmax", traction=(0.0, 0.0, -10.0),
+        steps=200, every=20, cfl=0.5, seed=0, tip_delta=1e-3, mass_rtol=1e-12, fd_rel_h=1e-6),
     "static_fab": dict(
         elems=(2, 2, 2), P=4, lengths=(1.0, 1.0, 1.0), E=1.0e3, nu=0.3, rho=1.0,
         clamp={"xmin": (0, 1, 2)}, k=0.5, lam=100.0),
