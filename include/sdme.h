@@ -384,6 +384,75 @@ sdme_status sdme_tangent_apply_noalloc(const sdme_mesh_desc* mesh, const sdme_ma
                                        const double* u_dev, double b1, const double* x_dev, double* y_dev,
                                        void* stream);
 
+/*
+ * Batches of independent problems (many meshes of uneven size, order and
+ * material solved together).  Each problem is a box mesh with its own
+ * order P (1..8) and material; the basis kind and its parameters are common
+ * (the P of `basis` is ignored).  Global vectors of all problems are
+ * concatenated: problem i's float64 vector (layout as for a context,
+ * [3][Nz][Ny][Nx]) starts at offset off[i] of a buffer of total_len entries
+ * (sdme_batch_layout); entries between segments are padding, kept zero.
+ *
+ * Every batched operation runs one launch per order group and step (not
+ * one per problem): the element kernels take up to 128 problems per launch
+ * with their scalars in the kernel parameter block, the per-DOF kernels
+ * split the grid among the problems, and PCG keeps one scalar block per
+ * problem so that each problem converges on its own; the PCG iterations are
+ * replayed in chunks as one captured CUDA graph for the whole batch.
+ */
+typedef struct {
+  sdme_mesh_desc mesh;
+  sdme_material mat;
+  int P;
+} sdme_problem;
+
+typedef struct sdme_batch sdme_batch;
+
+/* stream: as for sdme_create.  SDME_EUNSUPPORTED if the basis lacks the
+ * mirror symmetry (see sdme_create); SDME_EINVAL for invalid descriptors. */
+sdme_status sdme_batch_create(sdme_batch** out, const sdme_problem* probs, int nprob, const sdme_basis_desc* basis,
+                              sdme_precision prec, void* cuda_stream);
+sdme_status sdme_batch_destroy(sdme_batch* b);
+
+/* total_len: entries of a concatenated vector; off[i], ndof[i] (nprob each,
+ * either may be NULL): segment offset and DOF count of problem i. */
+sdme_status sdme_batch_layout(const sdme_batch* b, int64_t* total_len, int64_t* off, int64_t* ndof);
+
+/* As sdme_internal_force / sdme_tangent_apply / sdme_traction_load, for
+ * every problem at once.  t_host: 3 * nprob traction components (problem
+ * i's traction at t_host[3 i]).  Synchronise. */
+sdme_status sdme_batch_internal_force(sdme_batch* b, const double* u_dev, double* R_dev);
+sdme_status sdme_batch_tangent_apply(sdme_batch* b, const double* u_dev, double b1, const double* x_dev,
+                                     double* y_dev);
+sdme_status sdme_batch_traction_load(sdme_batch* b, int face, const double* t_host, double* f_dev);
+
+/*
+ * One implicit Newmark step of every problem (as sdme_implicit_newmark_step,
+ * same options for all).  Each problem runs its own Newton iteration and
+ * stops at its own tolerance; stats (nprob entries, may be NULL) receive
+ * each problem's record.  Returns SDME_OK when every problem converged,
+ * else the first failing problem's status.
+ */
+sdme_status sdme_batch_newmark_step(sdme_batch* b, sdme_state* state, double dt, const double* P_next_dev,
+                                    const sdme_newton_opts* opts, sdme_step_stats* stats);
+
+/*
+ * Launch-configuration tuner: for each order group, times the tangent
+ * launch (the PCG's dominant kernel) on the batch's own problems, reps
+ * launches per candidate, over one CTA per element and persistent grids of
+ * 1, 2 and 4 CTAs per SM times the kernel's resident CTAs per SM, and keeps
+ * the fastest for that order (for all element kernels of the group).  Needs
+ * a linearisation state (call after any batched residual, tangent apply or
+ * step).  orders/grids/ms (ngroups_max entries each, may be NULL) receive
+ * each group's order, chosen grid (0 = one CTA per element) and time per
+ * launch; *ngroups the number of groups.
+ */
+sdme_status sdme_batch_tune(sdme_batch* b, int reps, int ngroups_max, int* ngroups, int* orders, int* grids,
+                            float* ms);
+
+/* Kernel launches issued by the batch so far (all kinds). */
+sdme_status sdme_batch_launches(const sdme_batch* b, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,9 @@ EXPORTS = ("sdme_status_string", "sdme_build_basis1d", "sdme_create", "sdme_dest
            "sdme_tangent_apply_noalloc", "sdme_cuda_error_string", "sdme_explicit_start", "sdme_explicit_step",
            "sdme_energy", "sdme_estimate_dt_crit", "sdme_body_load", "sdme_mass_solve", "sdme_gauss_points",
            "sdme_set_material", "sdme_internal_force_vjp", "sdme_tape_create", "sdme_tape_destroy",
-           "sdme_explicit_forward", "sdme_explicit_adjoint")
+           "sdme_explicit_forward", "sdme_explicit_adjoint", "sdme_batch_create", "sdme_batch_destroy",
+           "sdme_batch_layout", "sdme_batch_internal_force", "sdme_batch_tangent_apply", "sdme_batch_traction_load",
+           "sdme_batch_newmark_step", "sdme_batch_tune", "sdme_batch_launches")
 
 
 class BasisDesc(ctypes.Structure):
@@ -47,6 +49,10 @@ class MeshDesc(ctypes.Structure):
 
 class Material(ctypes.Structure):
     _fields_ = [("mu", ctypes.c_double), ("lam", ctypes.c_double), ("rho", ctypes.c_double)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("mesh", MeshDesc), ("mat", Material), ("P", ctypes.c_int)]
 
 
 class NewtonOpts(ctypes.Structure):
@@ -114,6 +120,18 @@ def _load():
     lib.sdme_tape_destroy.argtypes = [vp]
     lib.sdme_explicit_forward.argtypes = [vp, vp, d, vp, vp, vp, pd, d, i, vp]
     lib.sdme_explicit_adjoint.argtypes = [vp, vp, vp, pd, pd, vp, vp, vp]
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.sdme_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Problem), i, ctypes.POINTER(BasisDesc), i, vp]
+    lib.sdme_batch_destroy.argtypes = [vp]
+    lib.sdme_batch_layout.argtypes = [vp, i64p, i64p, i64p]
+    lib.sdme_batch_internal_force.argtypes = [vp, vp, vp]
+    lib.sdme_batch_tangent_apply.argtypes = [vp, vp, d, vp, vp]
+    lib.sdme_batch_traction_load.argtypes = [vp, i, pd, vp]
+    lib.sdme_batch_newmark_step.argtypes = [vp, ctypes.POINTER(State), d, vp, ctypes.POINTER(NewtonOpts),
+                                            ctypes.POINTER(StepStats)]
+    lib.sdme_batch_tune.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                    ctypes.POINTER(ctypes.c_float)]
+    lib.sdme_batch_launches.argtypes = [vp, i64p]
     lib.sdme_set_timing.argtypes = [vp, i]
     lib.sdme_get_timing.argtypes = [vp, ctypes.POINTER(Timing)]
     lib.sdme_tangent_apply_noalloc.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(Material), i, pd, pd, pd,
@@ -201,6 +219,14 @@ def tangent_apply_noalloc(elems, lengths, clamp, mu, lam, rho, P, tables, u, b1,
                                                  float(b1), _ptr(x), _ptr(y), ctypes.c_void_p(stream.cuda_stream)),
                   "sdme_tangent_apply_noalloc", "sdme_cuda_error_string", "sdme_explicit_start", "sdme_explicit_step",
            "sdme_energy", "sdme_estimate_dt_crit", "sdme_body_load", "sdme_mass_solve", "sdme_gauss_points")
+
+
+def _stats_dict(stats, status):
+    n = min(stats.newton_iters, 32)
+    return {"status": status, "newton_iters": stats.newton_iters, "pcg_iters_total": stats.pcg_iters_total,
+            "matvecs": stats.matvecs, "converged": bool(stats.converged), "residual0": stats.residual0,
+            "residual_final": stats.residual_final, "pcg_iters": list(stats.pcg_iters[:n]),
+            "residuals": list(stats.residuals[:n + 1])}
 
 
 class _ExplicitStateHolder:
@@ -304,11 +330,7 @@ class Context:
         status = lib.sdme_implicit_newmark_step(self._h, ctypes.byref(st), float(dt), _ptr(P_next),
                                                 ctypes.byref(opts), ctypes.byref(stats))
         _check(status, "sdme_implicit_newmark_step", allow=allow, ctx=self._h)
-        n = min(stats.newton_iters, 32)
-        return {"status": status, "newton_iters": stats.newton_iters, "pcg_iters_total": stats.pcg_iters_total,
-                "matvecs": stats.matvecs, "converged": bool(stats.converged), "residual0": stats.residual0,
-                "residual_final": stats.residual_final, "pcg_iters": list(stats.pcg_iters[:n]),
-                "residuals": list(stats.residuals[:n + 1])}
+        return _stats_dict(stats, status)
 
     # -- explicit central difference (Sec. 4.1) ------------------------------
     def explicit_state(self, u, u_prev, a):
@@ -526,3 +548,91 @@ def explicit_trajectory(tape, dt, u0, v0, mu, lam, f=None, s=None, rtol=1e-12):
     if _trajectory_fn is None:
         _trajectory_fn = _TrajectoryFunction()
     return _trajectory_fn.apply(tape, dt, s, rtol, u0, v0, f, mu, lam)
+
+
+class Batch:
+    """Owns an sdme_batch: independent box-mesh problems solved together.
+    ``problems``: iterable of dicts with keys elems, lengths, clamp, mu, lam,
+    rho, P.  Vectors are concatenated float64 CUDA tensors of ``total`` entries;
+    problem i occupies [offsets[i], offsets[i] + ndofs[i])."""
+
+    def __init__(self, problems, kind, precision=FP64, k=0.5, lam_h=100.0, start_nodal=False, stream=None):
+        import torch
+        problems = list(problems)
+        arr = (Problem * len(problems))()
+        for j, pr in enumerate(problems):
+            arr[j].mesh = mesh_desc(pr["elems"], pr["lengths"], pr["clamp"])
+            arr[j].mat = Material(float(pr["mu"]), float(pr["lam"]), float(pr.get("rho", 1.0)))
+            arr[j].P = int(pr["P"])
+        self._basis = basis_desc(1, kind, k, lam_h, start_nodal)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.sdme_batch_create(ctypes.byref(h), arr, len(problems), ctypes.byref(self._basis), int(precision),
+                                     ctypes.c_void_p(stream.cuda_stream)), "sdme_batch_create")
+        self._h = h
+        self.nprob = len(problems)
+        tot = ctypes.c_int64()
+        off = (ctypes.c_int64 * self.nprob)()
+        nd = (ctypes.c_int64 * self.nprob)()
+        _check(lib.sdme_batch_layout(h, ctypes.byref(tot), off, nd), "sdme_batch_layout")
+        self.total, self.offsets, self.ndofs = tot.value, list(off), list(nd)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.sdme_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def zeros(self):
+        import torch
+        return torch.zeros(self.total, dtype=torch.float64, device="cuda")
+
+    def segment(self, v, i):
+        return v[self.offsets[i]:self.offsets[i] + self.ndofs[i]]
+
+    def internal_force(self, u, R):
+        return _check(lib.sdme_batch_internal_force(self._h, _ptr(u), _ptr(R)), "sdme_batch_internal_force")
+
+    def tangent_apply(self, u, b1, x, y):
+        return _check(lib.sdme_batch_tangent_apply(self._h, _ptr(u), float(b1), _ptr(x), _ptr(y)),
+                      "sdme_batch_tangent_apply")
+
+    def traction_load(self, face, t, f):
+        """t: sequence of nprob 3-vectors (or one 3-vector for all)."""
+        import numpy as np
+        t = np.ascontiguousarray(np.broadcast_to(np.asarray(t, dtype=np.float64), (self.nprob, 3)))
+        face = FACE_NAMES[face] if isinstance(face, str) else int(face)
+        return _check(lib.sdme_batch_traction_load(self._h, face, t.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                   _ptr(f)), "sdme_batch_traction_load")
+
+    def newmark_step(self, u, v, a, dt, P_next, beta=0.25, gamma=0.5, newton_tol=1e-8, max_newton=30,
+                     pcg_rtol=1e-10, mixed_rtol=1e-4, pcg_maxit=20000, allow=()):
+        st = State(u.data_ptr(), v.data_ptr(), a.data_ptr())
+        for t in (u, v, a):
+            _ptr(t)
+        opts = NewtonOpts(beta, gamma, newton_tol, max_newton, pcg_rtol, mixed_rtol, pcg_maxit)
+        stats = (StepStats * self.nprob)()
+        status = lib.sdme_batch_newmark_step(self._h, ctypes.byref(st), float(dt), _ptr(P_next), ctypes.byref(opts),
+                                             stats)
+        _check(status, "sdme_batch_newmark_step", allow=allow)
+        return [_stats_dict(s, status) for s in stats]
+
+    def tune(self, reps=5):
+        """Launch-configuration tuner; returns [(P, grid, ms per launch)] per order group."""
+        m = 16
+        ng = ctypes.c_int()
+        orders, grids, ms = (ctypes.c_int * m)(), (ctypes.c_int * m)(), (ctypes.c_float * m)()
+        _check(lib.sdme_batch_tune(self._h, int(reps), m, ctypes.byref(ng), orders, grids, ms), "sdme_batch_tune")
+        return [(orders[j], grids[j], ms[j]) for j in range(min(ng.value, m))]
+
+    def launches(self):
+        n = ctypes.c_int64()
+        _check(lib.sdme_batch_launches(self._h, ctypes.byref(n)), "sdme_batch_launches")
+        return n.value

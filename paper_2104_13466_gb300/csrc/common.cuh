@@ -142,6 +142,21 @@ __device__ __forceinline__ bool last_block_done(unsigned int* counter) {
   return last_;
 }
 
+// As last_block_done, for `total` arrivals that need not equal the grid
+// size (several problems per launch, or CTAs looping over elements).
+__device__ __forceinline__ bool last_arrival(unsigned int* counter, unsigned int total) {
+  __shared__ bool last_a_;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int t = atomicAdd(counter, 1u);
+    last_a_ = (t == total - 1);
+  }
+  __syncthreads();
+  if (last_a_) __threadfence();
+  return last_a_;
+}
+
 // Deterministic sum of m partials (fixed strided order + fixed tree).
 __device__ __forceinline__ double ordered_sum(const double* part, int m) {
   double s = 0.0;

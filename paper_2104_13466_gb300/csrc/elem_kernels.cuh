@@ -44,9 +44,10 @@ struct ElemTables {
   T DM[QH];
 };
 
-template <typename T, int P>
-struct ElemParams {
-  ElemTables<T, P> tab;
+// Per-mesh scalars of an element kernel (one problem of a batch, or the
+// whole mesh of a context).
+template <typename T>
+struct MeshParams {
   T s[3];        // 2 / h_d: reference-to-physical derivative scale
   T detJ;        // h_x h_y h_z / 8
   T mu, lam, rho;
@@ -55,6 +56,11 @@ struct ElemParams {
   int N[3];      // lattice points per direction
   int64_t Nn;    // lattice points (per component)
   unsigned clamp[6];
+};
+
+template <typename T, int P>
+struct ElemParams : MeshParams<T> {
+  ElemTables<T, P> tab;
   int pairs;     // 1: nodal basis, pair mirrored internal nodes on the fly
 };
 
@@ -493,27 +499,24 @@ __device__ __forceinline__ int64_t entry_index(const Prm& p, const ElemView<Prm>
 // (first Piola form of eq. second Piolla_Kirchhoff relation).
 //-----------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(elem_threads(P))
-residual_kernel(const __grid_constant__ ElemParams<double, P> prm, const double* __restrict__ u,
-                double* __restrict__ y, double* __restrict__ st64, float* __restrict__ st32,
-                int* __restrict__ err) {
+__device__ __forceinline__ void residual_body(const ElemTables<double, P>& tb, int pairs, const MeshParams<double>& m,
+                                              int e, const double* __restrict__ u, double* __restrict__ y,
+                                              double* __restrict__ st64, float* __restrict__ st32,
+                                              int* __restrict__ err, double* sm) {
   using T = double;
   using G = Geo<P>;
   constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
   T* X = sm + 3 * FQ;
-  const int e = blockIdx.x;
-  const ElemView<ElemParams<double, P>> view(prm, P, e);
+  const ElemView<MeshParams<double>> view(m, P, e);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
     int so;
-    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
+    const int64_t g = entry_index<P>(m, view, idx, &cons, &so);
     X[so] = u[g];
   }
   __syncthreads();
-  forward_stages<T, P, true>(prm.tab, prm.pairs, sm);
-  const T sc[3] = {prm.s[0], prm.s[1], prm.s[2]};
+  forward_stages<T, P, true>(tb, pairs, sm);
+  const T sc[3] = {m.s[0], m.s[1], m.s[2]};
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
     const int so = (qz * Q + qy) * XQ + qx;
@@ -536,15 +539,15 @@ residual_kernel(const __grid_constant__ ElemParams<double, P> prm, const double*
     if (!(J > T(0))) atomicOr(err, 1);
     const T iJ = T(1) / J;
     const T lnJ = log(J);
-    const T wdet = prm.tab.W[qx] * prm.tab.W[qy] * prm.tab.W[qz] * prm.detJ;
-    const T a = prm.lam * lnJ;
-    const T cst = prm.mu - a;
+    const T wdet = tb.W[qx] * tb.W[qy] * tb.W[qz] * m.detJ;
+    const T a = m.lam * lnJ;
+    const T cst = m.mu - a;
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const T H = cof[c][d] * iJ;  // (F^{-T})_cd
-        const T Pcd = prm.mu * (F[c][d] - H) + a * H;
+        const T Pcd = m.mu * (F[c][d] - H) + a * H;
         sm[(3 + 3 * d + c) * FQ + so] = wdet * Pcd * sc[d];
         const int64_t o = ((int64_t)e * kStateFields + (c * 3 + d)) * Q3 + q;
         if (st64) st64[o] = H;
@@ -553,18 +556,27 @@ residual_kernel(const __grid_constant__ ElemParams<double, P> prm, const double*
     const int64_t o = ((int64_t)e * kStateFields + 9) * Q3 + q;
     if (st64) st64[o] = cst;
     if (st32) st32[o] = (float)cst;
-    const T mfac = prm.b1 * prm.rho * wdet;
+    const T mfac = m.b1 * m.rho * wdet;
 #pragma unroll
     for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= mfac;
   }
   __syncthreads();
-  transpose_stages<T, P, true>(prm.tab, prm.pairs, sm);
+  transpose_stages<T, P, true>(tb, pairs, sm);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
     int so;
-    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
+    const int64_t g = entry_index<P>(m, view, idx, &cons, &so);
     atomicAdd(&y[g], X[so]);
   }
+}
+
+template <int P>
+__global__ void __launch_bounds__(elem_threads(P))
+residual_kernel(const __grid_constant__ ElemParams<double, P> prm, const double* __restrict__ u,
+                double* __restrict__ y, double* __restrict__ st64, float* __restrict__ st32,
+                int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  residual_body<P>(prm.tab, prm.pairs, prm, blockIdx.x, u, y, st64, st32, err, reinterpret_cast<double*>(smem_raw));
 }
 
 //-----------------------------------------------------------------------------
@@ -584,34 +596,34 @@ constexpr int tangent_min_blocks() {
 
 // STIFF = false gives the mass-only operator y += b1 M x (same masking and
 // PCG coupling, no linearisation state): the explicit scheme's system matrix.
-template <int P, typename T, typename TV, bool STIFF = true>
-__global__ void __launch_bounds__(elem_threads(P), tangent_min_blocks<T>())
-tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restrict__ x,
-               TV* __restrict__ y, const T* __restrict__ st, double* __restrict__ dot_partial,
-               PcgScalars* __restrict__ scal) {
+// dot_partial / scal (both optional) couple the launch to one PCG solve:
+// dot_partial[e] receives x_e . (K_e x_e), and the last of the nparts
+// elements to finish writes p.q and the step length into *scal.
+template <int P, typename T, typename TV, bool STIFF>
+__device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pairs, const MeshParams<T>& m, int e,
+                                             const TV* __restrict__ x, TV* __restrict__ y,
+                                             const T* __restrict__ st, double* __restrict__ dot_partial,
+                                             unsigned nparts, PcgScalars* __restrict__ scal, T* sm) {
   using G = Geo<P>;
   constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
   if (scal && scal->status != 0) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
   T* X = sm + 3 * FQ;
-  const int e = blockIdx.x;
-  const ElemView<ElemParams<T, P>> view(prm, P, e);
+  const ElemView<MeshParams<T>> view(m, P, e);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
     int so;
-    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
+    const int64_t g = entry_index<P>(m, view, idx, &cons, &so);
     X[so] = cons ? T(0) : (T)x[g];
   }
   __syncthreads();
-  forward_stages<T, P, STIFF>(prm.tab, prm.pairs, sm);
-  const T sc[3] = {prm.s[0], prm.s[1], prm.s[2]};
+  forward_stages<T, P, STIFF>(tb, pairs, sm);
+  const T sc[3] = {m.s[0], m.s[1], m.s[2]};
   const T* ste = st + (int64_t)e * kStateFields * Q3;
   if constexpr (!STIFF) {
     for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
       const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
       const int so = (qz * Q + qy) * XQ + qx;
-      const T mfac = prm.b1 * prm.rho * prm.tab.W[qx] * prm.tab.W[qy] * prm.tab.W[qz] * prm.detJ;
+      const T mfac = m.b1 * m.rho * tb.W[qx] * tb.W[qy] * tb.W[qz] * m.detJ;
 #pragma unroll
       for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= mfac;
     }
@@ -639,27 +651,27 @@ tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restric
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int j = 0; j < 3; ++j) W[a][j] = dF[0][a] * H[0][j] + dF[1][a] * H[1][j] + dF[2][a] * H[2][j];
-    const T wdet = prm.tab.W[qx] * prm.tab.W[qy] * prm.tab.W[qz] * prm.detJ;
-    const T ltr = prm.lam * tr;
+    const T wdet = tb.W[qx] * tb.W[qy] * tb.W[qz] * m.detJ;
+    const T ltr = m.lam * tr;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         const T V = H[i][0] * W[0][j] + H[i][1] * W[1][j] + H[i][2] * W[2][j];
-        const T dP = prm.mu * dF[i][j] + cst * V + ltr * H[i][j];
+        const T dP = m.mu * dF[i][j] + cst * V + ltr * H[i][j];
         sm[(3 + 3 * j + i) * FQ + so] = wdet * dP * sc[j];
       }
-    const T mfac = prm.b1 * prm.rho * wdet;
+    const T mfac = m.b1 * m.rho * wdet;
 #pragma unroll
     for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= mfac;
   }
   __syncthreads();
-  transpose_stages<T, P, STIFF>(prm.tab, prm.pairs, sm);
+  transpose_stages<T, P, STIFF>(tb, pairs, sm);
   T dotT = T(0);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
     int so;
-    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
+    const int64_t g = entry_index<P>(m, view, idx, &cons, &so);
     if (!cons) {
       const T v = X[so];
       atomicAdd(&y[g], (TV)v);
@@ -672,8 +684,8 @@ tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restric
     // fixed-order (deterministic) finalize by the last CTA to finish.
     const double tot = static_cast<double>(block_sum_t(dotT));
     if (threadIdx.x == 0) dot_partial[e] = tot;
-    if (scal && last_block_done(&scal->counter)) {
-      const double pq = ordered_sum(dot_partial, gridDim.x);
+    if (scal && last_arrival(&scal->counter, nparts)) {
+      const double pq = ordered_sum(dot_partial, (int)nparts);
       if (threadIdx.x == 0) {
         scal->pq = pq;
         scal->alpha = scal->rz / pq;
@@ -684,43 +696,57 @@ tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restric
   }
 }
 
+template <int P, typename T, typename TV, bool STIFF = true>
+__global__ void __launch_bounds__(elem_threads(P), tangent_min_blocks<T>())
+tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restrict__ x,
+               TV* __restrict__ y, const T* __restrict__ st, double* __restrict__ dot_partial,
+               PcgScalars* __restrict__ scal) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  tangent_body<P, T, TV, STIFF>(prm.tab, prm.pairs, prm, blockIdx.x, x, y, st, dot_partial, gridDim.x, scal,
+                                reinterpret_cast<T*>(smem_raw));
+}
+
 //-----------------------------------------------------------------------------
 // Mass: y += M x (no Dirichlet treatment).
 //-----------------------------------------------------------------------------
 template <int P, typename T>
-__global__ void __launch_bounds__(elem_threads(P))
-mass_kernel(const __grid_constant__ ElemParams<T, P> prm, const double* __restrict__ x,
-            double* __restrict__ y) {
+__device__ __forceinline__ void mass_body(const ElemTables<T, P>& tb, int pairs, const MeshParams<T>& m, int e,
+                                          const double* __restrict__ x, double* __restrict__ y, T* sm) {
   using G = Geo<P>;
   constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
   T* X = sm + 3 * FQ;
-  const int e = blockIdx.x;
-  const ElemView<ElemParams<T, P>> view(prm, P, e);
+  const ElemView<MeshParams<T>> view(m, P, e);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
     int so;
-    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
+    const int64_t g = entry_index<P>(m, view, idx, &cons, &so);
     X[so] = (T)x[g];
   }
   __syncthreads();
-  forward_stages<T, P, false>(prm.tab, prm.pairs, sm);
+  forward_stages<T, P, false>(tb, pairs, sm);
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
     const int so = (qz * Q + qy) * XQ + qx;
-    const T f = prm.rho * prm.tab.W[qx] * prm.tab.W[qy] * prm.tab.W[qz] * prm.detJ;
+    const T f = m.rho * tb.W[qx] * tb.W[qy] * tb.W[qz] * m.detJ;
 #pragma unroll
     for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= f;
   }
   __syncthreads();
-  transpose_stages<T, P, false>(prm.tab, prm.pairs, sm);
+  transpose_stages<T, P, false>(tb, pairs, sm);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
     int so;
-    const int64_t g = entry_index<P>(prm, view, idx, &cons, &so);
+    const int64_t g = entry_index<P>(m, view, idx, &cons, &so);
     atomicAdd(&y[g], (double)X[so]);
   }
+}
+
+template <int P, typename T>
+__global__ void __launch_bounds__(elem_threads(P))
+mass_kernel(const __grid_constant__ ElemParams<T, P> prm, const double* __restrict__ x,
+            double* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  mass_body<P, T>(prm.tab, prm.pairs, prm, blockIdx.x, x, y, reinterpret_cast<T*>(smem_raw));
 }
 
 //-----------------------------------------------------------------------------
@@ -737,41 +763,39 @@ constexpr int diag_smem_words() {
 }
 
 template <int P, typename T>
-__global__ void __launch_bounds__(elem_threads(P))
-diag_kernel(const __grid_constant__ ElemParams<T, P> prm, const T* __restrict__ st, T* __restrict__ y) {
+__device__ __forceinline__ void diag_body(const ElemTables<T, P>& tb, const MeshParams<T>& m, int e,
+                                          const T* __restrict__ st, T* __restrict__ y, T* smem) {
   constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q;
   // field f: (d, d') pairs then the mass field
   constexpr int fd[7] = {0, 1, 2, 0, 0, 1, -1};
   constexpr int fe[7] = {0, 1, 2, 1, 2, 2, -1};
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* F7 = reinterpret_cast<T*>(smem_raw);      // [7][Q^3], later S1 [7][n][n][Q]
+  T* F7 = smem;                                // [7][Q^3], later S1 [7][n][n][Q]
   T* S2 = F7 + 7 * Q3;                         // [7][n][Q][Q]
   T* TB = S2 + 7 * n * Q * Q;                  // BB, BD, DD: [3][Q][n]
   for (int i = threadIdx.x; i < Q * n; i += blockDim.x) {
-    const T b = prm.tab.B[i], d = prm.tab.D[i];
+    const T b = tb.B[i], d = tb.D[i];
     TB[i] = b * b;
     TB[Q * n + i] = b * d;
     TB[2 * Q * n + i] = d * d;
   }
-  const int e = blockIdx.x;
-  const int ex = e % prm.ne[0], ey = (e / prm.ne[0]) % prm.ne[1], ez = e / (prm.ne[0] * prm.ne[1]);
+  const int ex = e % m.ne[0], ey = (e / m.ne[0]) % m.ne[1], ez = e / (m.ne[0] * m.ne[1]);
   const T* ste = st + (int64_t)e * kStateFields * Q3;
-  const T sc[3] = {prm.s[0], prm.s[1], prm.s[2]};
+  const T sc[3] = {m.s[0], m.s[1], m.s[2]};
   for (int c = 0; c < 3; ++c) {
     __syncthreads();
     for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
-      const T wdet = wprod(prm.tab.W, q, Q) * prm.detJ;
-      const T a = ste[9 * Q3 + q] + prm.lam;
+      const T wdet = wprod(tb.W, q, Q) * m.detJ;
+      const T a = ste[9 * Q3 + q] + m.lam;
       const T h[3] = {ste[(c * 3 + 0) * Q3 + q], ste[(c * 3 + 1) * Q3 + q], ste[(c * 3 + 2) * Q3 + q]};
 #pragma unroll
       for (int f = 0; f < 6; ++f) {
         const int d = fd[f], d2 = fe[f];
         T v = a * h[d] * h[d2];
-        if (d == d2) v += prm.mu;
+        if (d == d2) v += m.mu;
         else v *= T(2);
         F7[f * Q3 + q] = wdet * sc[d] * sc[d2] * v;
       }
-      F7[6 * Q3 + q] = prm.b1 * prm.rho * wdet;
+      F7[6 * Q3 + q] = m.b1 * m.rho * wdet;
     }
     __syncthreads();
     // axis 2 (z): [f][Q][Q][Q] -> S2 [f][n][Q][Q]
@@ -810,8 +834,8 @@ diag_kernel(const __grid_constant__ ElemParams<T, P> prm, const T* __restrict__ 
     }
     __syncthreads();
     // axis 0 (x): sum over fields, one thread per output
-    for (int m = threadIdx.x; m < n3; m += blockDim.x) {
-      const int p = m % n, rq = m / n;   // rq = r*n + q
+    for (int mm = threadIdx.x; mm < n3; mm += blockDim.x) {
+      const int p = mm % n, rq = mm / n;   // rq = r*n + q
       T acc = T(0);
 #pragma unroll
       for (int f = 0; f < 7; ++f) {
@@ -821,10 +845,17 @@ diag_kernel(const __grid_constant__ ElemParams<T, P> prm, const T* __restrict__ 
         for (int a = 0; a < Q; ++a) acc += tab[a * n + p] * S1[f * n * n * Q + rq * Q + a];
       }
       bool cons;
-      int64_t g = dof_index(prm, P, ex, ey, ez, c * n3 + m, &cons);
+      int64_t g = dof_index(m, P, ex, ey, ez, c * n3 + mm, &cons);
       if (!cons) atomicAdd(&y[g], acc);
     }
   }
+}
+
+template <int P, typename T>
+__global__ void __launch_bounds__(elem_threads(P))
+diag_kernel(const __grid_constant__ ElemParams<T, P> prm, const T* __restrict__ st, T* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  diag_body<P, T>(prm.tab, prm, blockIdx.x, st, y, reinterpret_cast<T*>(smem_raw));
 }
 
 //-----------------------------------------------------------------------------

@@ -28,6 +28,39 @@ struct HostElemData {
   unsigned clamp[6] = {0, 0, 0, 0, 0, 0};
 };
 
+// Per-problem scalars of a batched launch (float64 on the host).
+struct HostMesh {
+  double s[3] = {0, 0, 0};
+  double detJ = 0, mu = 0, lam = 0, rho = 0;
+  int ne[3] = {0, 0, 0};
+  int N[3] = {0, 0, 0};
+  int64_t Nn = 0;
+  unsigned clamp[6] = {0, 0, 0, 0, 0, 0};
+};
+
+// One batched element launch: up to kBatchLaunchMax problems of one order.
+struct HostBatchLaunch {
+  std::vector<int> estart;                  // element prefix, size nprob + 1
+  std::vector<int> pid;                     // problem index in the batch
+  std::vector<int64_t> dof_off, st_off, part_off;
+  std::vector<HostMesh> mesh;
+};
+
+template <int P>
+cudaError_t launch_batch_residual(const HostElemData& tabs, const HostBatchLaunch& L, double b1, int grid,
+                                  const double* u, double* y, double* st64, float* st32, int* err, cudaStream_t s);
+template <int P, typename T, typename TV>
+cudaError_t launch_batch_tangent(const HostElemData& tabs, const HostBatchLaunch& L, double b1, int grid,
+                                 const TV* x, TV* y, const T* st, double* partial, PcgScalars* scal, cudaStream_t s);
+template <int P, typename T, typename TV>
+int batch_tangent_occupancy();
+template <int P, typename T>
+cudaError_t launch_batch_diag(const HostElemData& tabs, const HostBatchLaunch& L, double b1, int grid, const T* st,
+                              T* y, cudaStream_t s);
+template <int P>
+cudaError_t launch_batch_mass(const HostElemData& tabs, const HostBatchLaunch& L, int grid, const double* x,
+                              double* y, cudaStream_t s);
+
 template <int P>
 cudaError_t launch_residual(const HostElemData& h, double b1, const double* u, double* y, double* st64,
                             float* st32, int* err, cudaStream_t s);

@@ -1,7 +1,9 @@
 // Element kernels instantiated for polynomial order P = 1.
+#include "batch_elem.cuh"
 #include "elem_adjoint.cuh"
 
 namespace sdme {
 SDME_INSTANTIATE_ORDER(1)
 SDME_INSTANTIATE_ADJOINT(1)
+SDME_INSTANTIATE_BATCH(1)
 }  // namespace sdme

@@ -1,7 +1,9 @@
 // Element kernels instantiated for polynomial order P = 2.
+#include "batch_elem.cuh"
 #include "elem_adjoint.cuh"
 
 namespace sdme {
 SDME_INSTANTIATE_ORDER(2)
 SDME_INSTANTIATE_ADJOINT(2)
+SDME_INSTANTIATE_BATCH(2)
 }  // namespace sdme

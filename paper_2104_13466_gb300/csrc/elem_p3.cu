@@ -1,7 +1,9 @@
 // Element kernels instantiated for polynomial order P = 3.
+#include "batch_elem.cuh"
 #include "elem_adjoint.cuh"
 
 namespace sdme {
 SDME_INSTANTIATE_ORDER(3)
 SDME_INSTANTIATE_ADJOINT(3)
+SDME_INSTANTIATE_BATCH(3)
 }  // namespace sdme

@@ -1,7 +1,9 @@
 // Element kernels instantiated for polynomial order P = 4.
+#include "batch_elem.cuh"
 #include "elem_adjoint.cuh"
 
 namespace sdme {
 SDME_INSTANTIATE_ORDER(4)
 SDME_INSTANTIATE_ADJOINT(4)
+SDME_INSTANTIATE_BATCH(4)
 }  // namespace sdme

@@ -1,7 +1,9 @@
 // Element kernels instantiated for polynomial order P = 6.
+#include "batch_elem.cuh"
 #include "elem_adjoint.cuh"
 
 namespace sdme {
 SDME_INSTANTIATE_ORDER(6)
 SDME_INSTANTIATE_ADJOINT(6)
+SDME_INSTANTIATE_BATCH(6)
 }  // namespace sdme

@@ -1,7 +1,9 @@
 // Element kernels instantiated for polynomial order P = 7.
+#include "batch_elem.cuh"
 #include "elem_adjoint.cuh"
 
 namespace sdme {
 SDME_INSTANTIATE_ORDER(7)
 SDME_INSTANTIATE_ADJOINT(7)
+SDME_INSTANTIATE_BATCH(7)
 }  // namespace sdme

@@ -1,7 +1,9 @@
 // Element kernels instantiated for polynomial order P = 8.
+#include "batch_elem.cuh"
 #include "elem_adjoint.cuh"
 
 namespace sdme {
 SDME_INSTANTIATE_ORDER(8)
 SDME_INSTANTIATE_ADJOINT(8)
+SDME_INSTANTIATE_BATCH(8)
 }  // namespace sdme

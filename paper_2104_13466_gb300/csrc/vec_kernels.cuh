@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kVecThreads) k_diag_finish(MeshInfo mi, TV* __
 }
 
 // psi = P + mhat - y (mhat may be null), 0 on constrained DOFs; out = ||psi||^2.
-__global__ void __launch_bounds__(kVecThreads) k_residual_combine(MeshInfo mi, const double* __restrict__ Pl,
+static __global__ void __launch_bounds__(kVecThreads) k_residual_combine(MeshInfo mi, const double* __restrict__ Pl,
                                                                   const double* __restrict__ mhat,
                                                                   const double* __restrict__ y,
                                                                   double* __restrict__ psi,
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kVecThreads) k_residual_combine(MeshInfo mi, c
 }
 
 // out = ||x||^2 (all DOFs)
-__global__ void __launch_bounds__(kVecThreads) k_norm2(int64_t n, const double* __restrict__ x,
+static __global__ void __launch_bounds__(kVecThreads) k_norm2(int64_t n, const double* __restrict__ x,
                                                        double* __restrict__ partial, unsigned int* counter,
                                                        double* out) {
   double s = 0.0;
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kVecThreads) k_norm2(int64_t n, const double* 
 }
 
 // ahat = b2 v + b3 a + b1 u_n, so that a(u) = b1 u - ahat (Newmark, Sec. 4.2)
-__global__ void __launch_bounds__(kVecThreads) k_newmark_ahat(int64_t n, const double* __restrict__ un,
+static __global__ void __launch_bounds__(kVecThreads) k_newmark_ahat(int64_t n, const double* __restrict__ un,
                                                               const double* __restrict__ v,
                                                               const double* __restrict__ a, double b1, double b2,
                                                               double b3, double* __restrict__ ahat) {
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kVecThreads) k_newmark_ahat(int64_t n, const d
 }
 
 // a_{n+1} = b1 u - ahat ; v_{n+1} = v_n + dt ((1 - gamma) a_n + gamma a_{n+1})
-__global__ void __launch_bounds__(kVecThreads) k_newmark_final(int64_t n, const double* __restrict__ u,
+static __global__ void __launch_bounds__(kVecThreads) k_newmark_final(int64_t n, const double* __restrict__ u,
                                                                const double* __restrict__ ahat, double b1,
                                                                double dt, double gamma, double* __restrict__ v,
                                                                double* __restrict__ a) {
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kVecThreads) k_to_double(int64_t n, const TV* 
 
 // Central-difference start-up (Sec. 4.1): u_prev = u0 - dt v0 + dt^2/2 a0 on
 // free DOFs, u0 on constrained ones.
-__global__ void __launch_bounds__(kVecThreads) k_cd_start(MeshInfo mi, const double* __restrict__ u,
+static __global__ void __launch_bounds__(kVecThreads) k_cd_start(MeshInfo mi, const double* __restrict__ u,
                                                           const double* __restrict__ v, const double* __restrict__ a,
                                                           double dt, double* __restrict__ u_prev) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kVecThreads) k_cd_start(MeshInfo mi, const dou
 
 // Central-difference update (eq. Motion_explicit2): out (holding u_{n-1})
 // <- 2 u_n - u_{n-1} + dt^2 a_n on free DOFs, u_n on constrained ones.
-__global__ void __launch_bounds__(kVecThreads) k_cd_update(MeshInfo mi, const double* __restrict__ u,
+static __global__ void __launch_bounds__(kVecThreads) k_cd_update(MeshInfo mi, const double* __restrict__ u,
                                                            const double* __restrict__ a, double dt2,
                                                            double* __restrict__ u_prev) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kVecThreads) k_cd_update(MeshInfo mi, const do
 }
 
 // out = x . y (float64, fixed-order finalize by the last CTA)
-__global__ void __launch_bounds__(kVecThreads) k_dot(int64_t n, const double* __restrict__ x,
+static __global__ void __launch_bounds__(kVecThreads) k_dot(int64_t n, const double* __restrict__ x,
                                                      const double* __restrict__ y, double* __restrict__ partial,
                                                      unsigned int* counter, double* out) {
   double s = 0.0;
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kVecThreads) k_dot(int64_t n, const double* __
 
 // Deterministic pseudo-random start vector in [-1, 1] (integer hash of the
 // index), zero on constrained DOFs.
-__global__ void __launch_bounds__(kVecThreads) k_fill_hash(MeshInfo mi, double* __restrict__ x, unsigned seed) {
+static __global__ void __launch_bounds__(kVecThreads) k_fill_hash(MeshInfo mi, double* __restrict__ x, unsigned seed) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
        g += (int64_t)gridDim.x * blockDim.x) {
     uint32_t h = (uint32_t)g * 2654435761u ^ seed;
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kVecThreads) k_fill_hash(MeshInfo mi, double* 
   }
 }
 
-__global__ void __launch_bounds__(kVecThreads) k_scale(int64_t n, double s, double* __restrict__ x) {
+static __global__ void __launch_bounds__(kVecThreads) k_scale(int64_t n, double s, double* __restrict__ x) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
     x[g] *= s;
 }
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kVecThreads) k_scale(int64_t n, double s, doub
 // DOFs and u_n on constrained ones (A: mass inverse on the free DOFs), so
 // g_n = dJ/du_n = [2 g_{n+1} - g_{n+2} | g_{n+1}] - dt^2 K_T(u_n) z_n with
 // z_n = A g_{n+1}.  out may alias g2 (element-wise in place).
-__global__ void __launch_bounds__(kVecThreads) k_adj_step(MeshInfo mi, const double* g1, const double* g2,
+static __global__ void __launch_bounds__(kVecThreads) k_adj_step(MeshInfo mi, const double* g1, const double* g2,
                                                           const double* __restrict__ Kz, double dt2, double* out) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
        g += (int64_t)gridDim.x * blockDim.x) {
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kVecThreads) k_adj_step(MeshInfo mi, const dou
 }
 
 // out = a x on free DOFs, 0 on constrained ones.
-__global__ void __launch_bounds__(kVecThreads) k_masked_scale(MeshInfo mi, const double* __restrict__ x, double a,
+static __global__ void __launch_bounds__(kVecThreads) k_masked_scale(MeshInfo mi, const double* __restrict__ x, double a,
                                                               double* __restrict__ out) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
        g += (int64_t)gridDim.x * blockDim.x)
@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(kVecThreads) k_masked_scale(MeshInfo mi, const
 // Adjoint of the start-up u_{-1} = u_0 - dt v_0 + dt^2/2 A (P_0 - R(u_0)) (free
 // DOFs): with g_{-1} = -g_1 on free DOFs and z = A g_{-1},
 // dJ/du_0 = g_0 + g_{-1} - dt^2/2 K_T(u_0) z and dJ/dv_0 = -dt g_{-1}.
-__global__ void __launch_bounds__(kVecThreads) k_adj_start(MeshInfo mi, const double* __restrict__ g0,
+static __global__ void __launch_bounds__(kVecThreads) k_adj_start(MeshInfo mi, const double* __restrict__ g0,
                                                            const double* __restrict__ g1,
                                                            const double* __restrict__ Kz, double half_dt2, double dt,
                                                            double* __restrict__ gu0, double* __restrict__ gv0) {

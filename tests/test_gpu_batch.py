@@ -1,0 +1,165 @@
+"""GPU parity of the batched path (many independent meshes of uneven size,
+order and material in one set of launches) against the oracle, problem by
+problem.  Tolerances as for a single context: float64 1e-10 for operators;
+Newmark steps 1e-9 (u) / 1e-8 (v) / 1e-7 (a) at Newton 1e-12; mixed
+operators 2e-5.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import solvers  # noqa: E402
+from oracle.assembly import Discretization  # noqa: E402
+from oracle.basis1d import Basis1D  # noqa: E402
+from oracle.hexmesh import BoxMesh  # noqa: E402
+from oracle.material import lame  # noqa: E402
+from synthetic import random_uniform, random_vector  # noqa: E402
+
+TOL64, TOL32 = 1e-10, 2e-5
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _problems(seed=0, n=7, orders=(1, 2, 3, 4, 5, 8), max_e=3):
+    """Seeded uneven problems: sides in 1..max_e elements, order from
+    `orders`, E in [5e2, 5e3], nu in [0.25, 0.45]; bottom face clamped."""
+    r = random_uniform(5 * n, seed, 0.0, 1.0).reshape(n, 5)
+    out = []
+    for i in range(n):
+        elems = tuple(1 + int(r[i, k] * max_e) % max_e for k in range(3))
+        P = orders[i % len(orders)]
+        mu, lam = lame(5e2 + 4.5e3 * r[i, 3], 0.25 + 0.2 * r[i, 4])
+        out.append(dict(elems=elems, lengths=(1.0, 0.8, 1.2), clamp={"zmin": (0, 1, 2)}, mu=mu, lam=lam, rho=1.0,
+                        P=P))
+    return out
+
+
+def _oracles(probs, kind):
+    ds = []
+    for pr in probs:
+        mesh = BoxMesh(*pr["elems"], pr["P"], lengths=pr["lengths"])
+        for f, c in pr["clamp"].items():
+            mesh.clamp(f, c)
+        ds.append(Discretization(mesh, Basis1D(pr["P"], kind), pr["mu"], pr["lam"], pr["rho"]))
+    return ds
+
+
+def _batch(probs, kind, prec=0):
+    import paper_2104_13466_gb300 as s
+    return s.Batch(probs, kind, precision=prec)
+
+
+def _random_state(b, ds, scale, seed):
+    u = np.zeros(b.total)
+    for i, d in enumerate(ds):
+        h = min(d.mesh.h) / d.mesh.P
+        u[b.offsets[i]:b.offsets[i] + b.ndofs[i]] = random_vector(b.ndofs[i], seed + i, scale * h)
+    return u
+
+
+@pytest.mark.parametrize("kind", ["sdme_h", "nodal"])
+def test_batch_internal_force_and_tangent_fp64(kind):
+    probs = _problems()
+    b = _batch(probs, kind)
+    ds = _oracles(probs, kind)
+    assert [d.mesh.ndof for d in ds] == b.ndofs
+    u = _random_state(b, ds, 0.05, 10)
+    x = random_vector(b.total, 3)
+    R = b.zeros()
+    b.internal_force(_dev(u), R)
+    y = b.zeros()
+    b.tangent_apply(_dev(u), 40.0, _dev(x), y)
+    Rh, yh = _host(R), _host(y)
+    for i, d in enumerate(ds):
+        seg = slice(b.offsets[i], b.offsets[i] + b.ndofs[i])
+        assert _rel(Rh[seg], d.internal_force(u[seg])) < TOL64, i
+        assert _rel(yh[seg], d.effective_apply(u[seg], x[seg], b1=40.0)) < TOL64, i
+    # padding between segments stays untouched
+    pad = np.ones(b.total, dtype=bool)
+    for i in range(b.nprob):
+        pad[b.offsets[i]:b.offsets[i] + b.ndofs[i]] = False
+    assert np.all(Rh[pad] == 0.0)
+
+
+def test_batch_tangent_mixed():
+    import paper_2104_13466_gb300 as s
+    probs = _problems(seed=1)
+    b = _batch(probs, "sdme_m", prec=s.MIXED_FP32)
+    ds = _oracles(probs, "sdme_m")
+    u = _random_state(b, ds, 0.05, 20)
+    x = random_vector(b.total, 4)
+    y = b.zeros()
+    b.tangent_apply(_dev(u), 10.0, _dev(x), y)
+    yh = _host(y)
+    for i, d in enumerate(ds):
+        seg = slice(b.offsets[i], b.offsets[i] + b.ndofs[i])
+        assert _rel(yh[seg], d.effective_apply(u[seg], x[seg], b1=10.0)) < TOL32, i
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_newmark_steps(prec):
+    probs = _problems(seed=2, n=5, orders=(2, 3, 4), max_e=2)
+    b = _batch(probs, "sdme_h", prec=prec)
+    ds = _oracles(probs, "sdme_h")
+    mags = [0.05 * pr["mu"] for pr in probs]
+    f = b.zeros()
+    b.traction_load("zmax", [(0.0, 0.0, -m) for m in mags], f)
+    fh = _host(f)
+    u, v, a = b.zeros(), b.zeros(), b.zeros()
+    states = [(np.zeros(d.mesh.ndof),) * 3 for d in ds]
+    dt = 0.01
+    for n in range(1, 3):
+        stats = b.newmark_step(u, v, a, dt, f * (n / 2.0), newton_tol=1e-12, pcg_rtol=1e-13, mixed_rtol=1e-5)
+        assert all(st["converged"] for st in stats)
+        for i, d in enumerate(ds):
+            seg = slice(b.offsets[i], b.offsets[i] + b.ndofs[i])
+            uo, vo, ao = states[i]
+            uo, vo, ao, so = solvers.newmark_step(d, uo, vo, ao, fh[seg] * (n / 2.0), dt, tol=1e-12, pcg_rtol=1e-13)
+            states[i] = (uo, vo, ao)
+    uh, vh, ah = _host(u), _host(v), _host(a)
+    for i in range(b.nprob):
+        seg = slice(b.offsets[i], b.offsets[i] + b.ndofs[i])
+        uo, vo, ao = states[i]
+        if prec == 0:
+            assert _rel(uh[seg], uo) < 1e-9 and _rel(vh[seg], vo) < 1e-8 and _rel(ah[seg], ao) < 1e-7, i
+        else:
+            assert _rel(uh[seg], uo) < 1e-8 and _rel(vh[seg], vo) < 1e-6, i
+    # each problem keeps its own Newton record
+    assert len(stats) == b.nprob and all(st["newton_iters"] >= 1 for st in stats)
+
+
+def test_batch_tuner_keeps_results():
+    probs = _problems(seed=3, n=6)
+    b = _batch(probs, "sdme_h")
+    ds = _oracles(probs, "sdme_h")
+    u = _random_state(b, ds, 0.05, 30)
+    x = random_vector(b.total, 5)
+    y0 = b.zeros()
+    b.tangent_apply(_dev(u), 5.0, _dev(x), y0)
+    tuned = b.tune(reps=2)
+    assert sorted(p for p, _, _ in tuned) == sorted({pr["P"] for pr in probs})
+    assert all(ms > 0 for _, _, ms in tuned)
+    y1 = b.zeros()
+    b.tangent_apply(_dev(u), 5.0, _dev(x), y1)
+    assert _rel(_host(y1), _host(y0)) < 1e-13
+
+
+def test_batch_rejects_invalid_problems():
+    import paper_2104_13466_gb300 as s
+    bad = _problems(n=2)
+    bad[1]["P"] = 9
+    with pytest.raises(s.SdmeError):
+        _batch(bad, "sdme_h")
