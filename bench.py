@@ -548,6 +548,134 @@ def run_adjoint(args, w):
     print(json.dumps(out), flush=True)
 
 
+def compare_sequential(args, w, probs, b_full, f_full, dt, steps):
+    """The first K problems of the batch solved (a) as one batch and (b) one
+    context at a time, `steps` Newmark steps each on identical inputs;
+    prints both wall times (the batching gain) and the largest difference
+    between the two solutions."""
+    import torch
+    import paper_2104_13466_gb300 as sd
+    K = args.batch_vs_sequential
+    sub = probs[:K]
+    prec = sd.MIXED_FP32 if args.precision == "mixed" else sd.FP64
+    fh = [b_full.segment(f_full, i).clone() for i in range(K)]
+    opts = dict(newton_tol=w["newton_tol"], mixed_rtol=args.mixed_rtol, pcg_maxit=args.pcg_maxit)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    b = sd.Batch(sub, args.basis, precision=prec, k=w["k"], lam_h=w["lam"])
+    if not args.no_tune:
+        b.tune(reps=3)
+    fb = b.zeros()
+    for i in range(K):
+        b.segment(fb, i).copy_(fh[i])
+
+    def run_batch():
+        u, v, a = b.zeros(), b.zeros(), b.zeros()
+        for n in range(1, steps + 1):
+            b.newmark_step(u, v, a, dt, fb * (n / w["steps"]), **opts)
+        return u
+
+    ctxs = [sd.Context(pr["elems"], pr["lengths"], pr["clamp"], pr["mu"], pr["lam"], pr["rho"], pr["P"], args.basis,
+                       precision=prec, k=w["k"], lam_h=w["lam"]) for pr in sub]
+
+    def run_seq():
+        us = []
+        for i, c in enumerate(ctxs):
+            u, v, a = (torch.zeros(c.ndof, dtype=torch.float64, device="cuda") for _ in range(3))
+            for n in range(1, steps + 1):
+                c.implicit_newmark_step(u, v, a, dt, fh[i] * (n / w["steps"]), **opts)
+            us.append(u)
+        return us
+
+    run_batch()  # warm-up
+    run_seq()
+    ub, t_batch = timed(run_batch)
+    us, t_seq = timed(run_seq)
+    diff = max(float((b.segment(ub, i) - us[i]).abs().max() / us[i].abs().max()) for i in range(K))
+    print(json.dumps({"mode": "batch-vs-sequential", "problems": K, "steps": steps, "dofs": int(sum(b.ndofs)),
+                      "batch_ms": t_batch, "sequential_ms": t_seq, "speedup": t_seq / t_batch,
+                      "max_rel_diff": diff}), flush=True)
+
+
+def run_batch(args, w):
+    """Batched independent solves (config 4 shape): 256 seeded cubes of uneven
+    size, order and material, each taking `steps` implicit Newmark steps of a
+    ramped top traction, all problems advanced together (one set of launches
+    per step, PCG chunks replayed as one CUDA graph for the whole batch), in
+    mixed precision (float32 tangent and PCG inside the float64 Newton
+    residual).  Reports the aggregate tangent-matvec DOF/s over the timed
+    steps, the wall time, and the tuner's launch configuration per order."""
+    import torch
+    import paper_2104_13466_gb300 as sd
+    from synthetic import batch_draws, load_magnitude
+    side, orders, E, nu = batch_draws(w)
+    probs = []
+    for i in range(w["count"]):
+        mu, lam = lame(E[i], nu[i])
+        probs.append(dict(elems=(side[i],) * 3, lengths=(1.0, 1.0, 1.0), clamp=w["clamp"], mu=mu, lam=lam,
+                          rho=w["rho"], P=orders[i]))
+    prec = sd.MIXED_FP32 if args.precision == "mixed" else sd.FP64
+    t0 = time.time()
+    b = sd.Batch(probs, args.basis, precision=prec, k=w["k"], lam_h=w["lam"])
+    t_create = time.time() - t0
+    smag = load_magnitude(w["load_key"])
+    f = b.zeros()
+    scale = (w["load_scale"] if args.batch_load_scale is None else args.batch_load_scale) * smag / 1.0e3
+    b.traction_load(w["traction_face"], [(0.0, 0.0, -scale * E[i]) for i in range(w["count"])], f)
+    tuning = b.tune(reps=3) if not args.no_tune else []
+    steps = args.batch_steps or w["steps"]
+    dt = w["dt"]
+
+    def run(nsteps, time_it):
+        u, v, a = b.zeros(), b.zeros(), b.zeros()
+        stats, ms = [], 0.0
+        for n in range(1, nsteps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            st = b.newmark_step(u, v, a, dt, f * (n / w["steps"]), newton_tol=w["newton_tol"],
+                                mixed_rtol=args.mixed_rtol, pcg_maxit=args.pcg_maxit,
+                                allow=(sd.NONPOSITIVE_J, sd.NEWTON_DIVERGED, sd.NAN))
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            stats.append(st)
+        return stats, ms
+
+    if args.batch_vs_sequential:
+        compare_sequential(args, w, probs, b, f, dt, steps=2)
+        b.close()
+        return
+    run(1, False)  # warm-up: kernel attributes, graph capture
+    l0 = b.launches()
+    stats, ms = run(steps, True)
+    launches = b.launches() - l0
+    dof_matvecs = sum(b.ndofs[i] * st[i]["matvecs"] for st in stats for i in range(b.nprob))
+    conv = all(st[i]["converged"] for st in stats for i in range(b.nprob))
+    failed = sorted({i for st in stats for i in range(b.nprob) if not st[i]["converged"]})
+    newton = [st[i]["newton_iters"] for st in stats for i in range(b.nprob)]
+    pcg = [st[i]["pcg_iters_total"] / max(1, st[i]["newton_iters"]) for st in stats for i in range(b.nprob)]
+    out = {"mode": "batch", "workload": args.workload, "basis": args.basis, "precision": args.precision,
+           "problems": b.nprob, "total_dofs": int(sum(b.ndofs)), "elements": int(sum(s_ ** 3 for s_ in side)),
+           "steps": steps, "dt": dt, "wall_ms": ms, "ms_per_step": ms / steps,
+           "matvec_dofs_per_s": dof_matvecs / (ms * 1e-3), "all_converged": conv,
+           "failed": [{"i": i, "side": side[i], "P": orders[i], "E": E[i], "nu": nu[i]} for i in failed][:20],
+           "newton_iters_mean": float(np.mean(newton)), "newton_iters_max": int(np.max(newton)),
+           "pcg_iters_per_newton_mean": float(np.mean(pcg)), "pcg_iters_per_newton_max": float(np.max(pcg)),
+           "gpu_launches": launches, "create_s": t_create,
+           "tuning": [{"P": p_, "grid": g_, "tangent_ms": m_} for p_, g_, m_ in tuning]}
+    b.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -573,11 +701,20 @@ def main():
     ap.add_argument("--precisions", default="mixed,fp64")
     ap.add_argument("--kernel-iters", type=int, default=20)
     ap.add_argument("--adjoint", action="store_true")
+    ap.add_argument("--batch", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--batch-load-scale", type=float, default=None)
+    ap.add_argument("--batch-vs-sequential", type=int, default=0)
     args = ap.parse_args()
+    if args.batch and args.workload == "beam_p8":
+        args.workload = "batch_cubes"
     if args.adjoint and args.workload == "beam_p8":
         args.workload = "beam_p6_adjoint"
     w = workload(args.workload)
-    if args.adjoint:
+    if args.batch:
+        run_batch(args, w)
+    elif args.adjoint:
         run_adjoint(args, w)
     elif args.kernel_only:
         run_kernel_only(args, w)

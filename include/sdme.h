@@ -429,9 +429,11 @@ sdme_status sdme_batch_traction_load(sdme_batch* b, int face, const double* t_ho
 /*
  * One implicit Newmark step of every problem (as sdme_implicit_newmark_step,
  * same options for all).  Each problem runs its own Newton iteration and
- * stops at its own tolerance; stats (nprob entries, may be NULL) receive
- * each problem's record.  Returns SDME_OK when every problem converged,
- * else the first failing problem's status.
+ * stops at its own tolerance; a problem that meets det F <= 0 or a PCG
+ * breakdown stops there while the others continue.  stats (nprob entries,
+ * may be NULL) receive each problem's record (converged = 0 for a problem
+ * that failed).  Returns SDME_OK when every problem converged, else the
+ * status of the first failing problem.
  */
 sdme_status sdme_batch_newmark_step(sdme_batch* b, sdme_state* state, double dt, const double* P_next_dev,
                                     const sdme_newton_opts* opts, sdme_step_stats* stats);

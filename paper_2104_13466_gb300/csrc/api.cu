@@ -253,6 +253,9 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, bool mass_only, const double* b, 
   ctx->kernel_launches += 1;
   int done_iters = 0;
   for (;;) {
+    // launch accounting: one executed chunk = kPcgChunk x (operator, update,
+    // direction); a capture issues launches that do not execute
+    const int64_t l0 = ctx->kernel_launches;
     // Per-launch event timing needs the events recorded by plain stream
     // launches (events recorded inside a graph cannot be queried), so the
     // timed mode issues the chunk directly; the untimed mode replays a graph.
@@ -283,7 +286,7 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, bool mass_only, const double* b, 
     } else {
       SDME_CUDA(cudaGraphLaunch(ge, ctx->stream));
     }
-    ctx->kernel_launches += 3 * kPcgChunk;
+    ctx->kernel_launches = l0 + 3 * kPcgChunk;
     SDME_CUDA(cudaMemcpyAsync(ctx->scal_h, ctx->scal, sizeof(PcgScalars), cudaMemcpyDeviceToHost, ctx->stream));
     SDME_CUDA(cudaStreamSynchronize(ctx->stream));
     const PcgScalars& s = *ctx->scal_h;

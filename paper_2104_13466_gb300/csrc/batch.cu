@@ -40,6 +40,7 @@ struct Group {
   HostElemData tabs;
   std::vector<int> probs;
   std::vector<HostBatchLaunch> launches;
+  std::vector<HostBatchLaunch> run_launches;  // launches restricted to the problems whose PCG is running
   int64_t nelem = 0;
   int grid = 0;      // 0: one CTA per element; else persistent CTAs
   float tuned_ms = 0.f;
@@ -102,6 +103,8 @@ struct sdme_batch {
   cudaGraphExec_t gexec = nullptr;
   double gb1 = 0.0;
   int gsize = 0;
+  std::vector<int> grun;      // running problems the captured chunk was built for
+  bool warm = false;          // kernels' attributes set (first chunk ran directly)
   int64_t launches = 0;
 };
 
@@ -201,8 +204,8 @@ const T* b_state(sdme_batch* b) {
 
 template <typename T, typename TV>
 sdme_status b_tangent_group(sdme_batch* b, Group& g, double b1, int grid, const TV* x, TV* y, double* partial,
-                            PcgScalars* scal) {
-  for (const HostBatchLaunch& L : g.launches) {
+                            PcgScalars* scal, bool running_only = false) {
+  for (const HostBatchLaunch& L : running_only ? g.run_launches : g.launches) {
     B_CUDA(dispatch_order(g.P, [&](auto Pc) {
       return launch_batch_tangent<decltype(Pc)::value, T, TV>(g.tabs, L, b1, grid, x, y, b_state<T>(b), partial,
                                                               scal, b->stream);
@@ -213,9 +216,38 @@ sdme_status b_tangent_group(sdme_batch* b, Group& g, double b1, int grid, const 
 }
 
 template <typename T, typename TV>
-sdme_status b_tangent(sdme_batch* b, double b1, const TV* x, TV* y, double* partial, PcgScalars* scal) {
-  for (Group& g : b->groups) B_TRY((b_tangent_group<T, TV>(b, g, b1, g.grid, x, y, partial, scal)));
+sdme_status b_tangent(sdme_batch* b, double b1, const TV* x, TV* y, double* partial, PcgScalars* scal,
+                      bool running_only = false) {
+  for (Group& g : b->groups)
+    B_TRY((b_tangent_group<T, TV>(b, g, b1, g.grid, x, y, partial, scal, running_only)));
   return SDME_OK;
+}
+
+// Element launches of every group restricted to the problems in `run`
+// (sorted), so that converged problems cost no CTAs in later iterations.
+void build_run_launches(sdme_batch* b, const std::vector<int>& run) {
+  std::vector<char> on(b->nprob, 0);
+  for (int i : run) on[i] = 1;
+  for (Group& g : b->groups) {
+    g.run_launches.clear();
+    for (const HostBatchLaunch& L : g.launches) {
+      HostBatchLaunch R;
+      int acc = 0;
+      for (size_t k = 0; k < L.pid.size(); ++k) {
+        if (!on[L.pid[k]]) continue;
+        R.estart.push_back(acc);
+        R.pid.push_back(L.pid[k]);
+        R.dof_off.push_back(L.dof_off[k]);
+        R.st_off.push_back(L.st_off[k]);
+        R.part_off.push_back(L.part_off[k]);
+        R.mesh.push_back(L.mesh[k]);
+        acc += L.estart[k + 1] - L.estart[k];
+      }
+      if (R.pid.empty()) continue;
+      R.estart.push_back(acc);
+      g.run_launches.push_back(R);
+    }
+  }
 }
 
 template <typename T>
@@ -266,7 +298,7 @@ struct BatchSideScope {
 template <typename T, typename TV>
 sdme_status b_pcg_chunk(sdme_batch* b, double b1, TV* r, TV* p, TV* q, TV* dinv, TV* xv) {
   for (int j = 0; j < kChunk; ++j) {
-    B_TRY((b_tangent<T, TV>(b, b1, p, q, b->partial, b->scal)));
+    B_TRY((b_tangent<T, TV>(b, b1, p, q, b->partial, b->scal, true)));
     kb_pcg_update<TV><<<b->vec_grid, kVecThreads, 0, b->stream>>>(b->info, b->cta_prob, xv, r, p, q, dinv, b->scal,
                                                                   b->partial);
     kb_pcg_direction<TV><<<b->vec_grid, kVecThreads, 0, b->stream>>>(b->info, b->cta_prob, r, dinv, p, b->scal);
@@ -287,14 +319,34 @@ sdme_status b_pcg(sdme_batch* b, double b1, const double* rhs, double* x_out, do
                                                               b->scal, b->partial, b->active, rtol, maxit);
   B_CUDA(cudaGetLastError());
   b->launches += 1;
-  if (b->gexec && (b->gb1 != b1 || b->gsize != (int)sizeof(T))) {
-    cudaGraphExecDestroy(b->gexec);
-    b->gexec = nullptr;
-  }
-  for (;;) {
-    if (!b->gexec) {
-      // the first chunk runs directly (kernel attributes), then is captured
-      B_TRY((b_pcg_chunk<T, TV>(b, b1, r, p, q, dinv, xv)));
+  auto read_status = [&](std::vector<int>& run) -> sdme_status {
+    B_CUDA(cudaMemcpyAsync(b->scal_h, b->scal, sizeof(PcgScalars) * b->nprob, cudaMemcpyDeviceToHost, b->stream));
+    B_CUDA(cudaStreamSynchronize(b->stream));
+    run.clear();
+    for (int i = 0; i < b->nprob; ++i)
+      if (b->scal_h[i].status == kPcgRunning) run.push_back(i);
+    return SDME_OK;
+  };
+  std::vector<int> run;
+  B_TRY(read_status(run));
+  while (!run.empty()) {
+    // the captured chunk covers the running problems only; it is rebuilt
+    // whenever that set (or the operator) changes.  Launch accounting: one
+    // executed chunk = kChunk x (element launches + update + direction).
+    const int64_t l0 = b->launches;
+    if (!b->gexec || run != b->grun || b->gb1 != b1 || b->gsize != (int)sizeof(T)) {
+      if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+      }
+      build_run_launches(b, run);
+      if (!b->warm) {  // the first chunk runs directly (sets the kernels' attributes)
+        B_TRY((b_pcg_chunk<T, TV>(b, b1, r, p, q, dinv, xv)));
+        b->warm = true;
+        B_TRY(read_status(run));
+        continue;
+      }
+      const int64_t lc = b->launches;
       cudaGraph_t g = nullptr;
       B_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
       sdme_status cs = b_pcg_chunk<T, TV>(b, b1, r, p, q, dinv, xv);
@@ -306,17 +358,14 @@ sdme_status b_pcg(sdme_batch* b, double b1, const double* rhs, double* x_out, do
       B_CUDA(ce);
       b->gb1 = b1;
       b->gsize = (int)sizeof(T);
-    } else {
-      B_CUDA(cudaGraphLaunch(b->gexec, b->stream));
-      int64_t per = 2 * kChunk;
-      for (const Group& g : b->groups) per += kChunk * (int64_t)g.launches.size();
-      b->launches += per;
+      b->grun = run;
+      b->launches = lc;  // captured, not executed
     }
-    B_CUDA(cudaMemcpyAsync(b->scal_h, b->scal, sizeof(PcgScalars) * b->nprob, cudaMemcpyDeviceToHost, b->stream));
-    B_CUDA(cudaStreamSynchronize(b->stream));
-    bool running = false;
-    for (int i = 0; i < b->nprob; ++i) running = running || b->scal_h[i].status == kPcgRunning;
-    if (!running) break;
+    B_CUDA(cudaGraphLaunch(b->gexec, b->stream));
+    int64_t per = 2 * kChunk;
+    for (const Group& g : b->groups) per += kChunk * (int64_t)g.run_launches.size();
+    b->launches = l0 + per;
+    B_TRY(read_status(run));
   }
   k_to_double<TV><<<kVecGridTotal, kVecThreads, 0, b->stream>>>(b->total, xv, 1.0, x_out);
   B_CUDA(cudaGetLastError());
@@ -604,7 +653,6 @@ sdme_status sdme_batch_newmark_step(sdme_batch* b, sdme_state* state, double dt,
     b->active_h[i] = 1;
   }
   const double inner_rtol = (b->prec == SDME_MIXED_FP32) ? o.mixed_rtol : o.pcg_rtol;
-  sdme_status hard = SDME_OK;
   for (int k = 0; k <= o.max_newton; ++k) {
     B_TRY(b_residual(b, b1, state->u, b->y));
     kb_residual_combine<<<b->vec_grid, kVecThreads, 0, s>>>(b->info, b->cta_prob, P_next_dev, b->mhat, b->y,
@@ -612,14 +660,19 @@ sdme_status sdme_batch_newmark_step(sdme_batch* b, sdme_state* state, double dt,
     B_CUDA(cudaGetLastError());
     b->launches += 1;
     B_CUDA(cudaMemcpyAsync(b->dnorm_h, b->dnorm, sizeof(double) * np, cudaMemcpyDeviceToHost, s));
-    const sdme_status je = b_check_err(b);
-    if (je != SDME_OK) {
-      hard = je;
-      break;
-    }
+    B_CUDA(cudaMemcpyAsync(b->err_h, b->err, sizeof(int) * np, cudaMemcpyDeviceToHost, s));
+    B_CUDA(cudaStreamSynchronize(s));
+    bool jbad = false;
+    for (int i = 0; i < np; ++i) jbad = jbad || b->err_h[i] != 0;
+    if (jbad) B_CUDA(cudaMemsetAsync(b->err, 0, sizeof(int) * np, s));
     bool any = false;
     for (int i = 0; i < np; ++i) {
       if (!b->active_h[i]) continue;
+      if (b->err_h[i]) {  // det F <= 0 somewhere in this problem: it stops here
+        res[i] = SDME_NONPOSITIVE_J;
+        b->active_h[i] = 0;
+        continue;
+      }
       const double nrm = std::sqrt(b->dnorm_h[i]);
       if (!std::isfinite(nrm)) {
         res[i] = SDME_NAN;
@@ -664,7 +717,7 @@ sdme_status sdme_batch_newmark_step(sdme_batch* b, sdme_state* state, double dt,
   B_CUDA(cudaGetLastError());
   b->launches += 1;
   B_CUDA(cudaStreamSynchronize(s));
-  sdme_status out = hard;
+  sdme_status out = SDME_OK;
   for (int i = 0; i < np; ++i) {
     st[i].residual0 = psi0[i];
     if (stats) stats[i] = st[i];

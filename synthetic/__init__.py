@@ -24,6 +24,13 @@ lambda = 100) scaled to the GPU problem sizes:
                 constant dead traction on x = 8, 200 steps at half the stable
                 step, checkpoints every 20 steps; objective = squared distance of
                 the final tip-face displacement to a seeded target.
+* ``batch_cubes``  256 independent unit cubes: n^3 hexes with n ~ U{2..12},
+                P uniform over {3, 4, 5, 6, 8}, E ~ U[5e2, 5e3], nu ~ U[0.25, 0.45]
+                (all from `seed`); bottom face clamped, uniform top traction
+                (half the cube_p4 magnitude, scaled by E / 1000) ramped over 20
+                implicit Newmark steps, dt = 0.01.  At the full magnitude the
+                finest nearly incompressible cube (12^3, P = 8, nu = 0.447)
+                inverts elements at its clamped bottom edges during the ramp.
 * ``static_fab``  the paper's static fabricated problem (Sec. 5.1): unit cube,
                 2x2x2 hexes, x = 0 clamped.
 
@@ -72,6 +79,10 @@ WORKLOADS = {
         elems=(32, 4, 4), P=6, lengths=(8.0, 1.0, 1.0), E=1.0e3, nu=0.3, rho=1.0,
         clamp={"xmin": (0, 1, 2)}, traction_face="xmax", traction=(0.0, 0.0, -10.0),
         steps=200, every=20, cfl=0.5, seed=0, tip_delta=1e-3, mass_rtol=1e-12, fd_rel_h=1e-6),
+    "batch_cubes": dict(
+        count=256, side=(2, 12), orders=(3, 4, 5, 6, 8), E=(5.0e2, 5.0e3), nu=(0.25, 0.45), rho=1.0, seed=0,
+        clamp={"zmin": (0, 1, 2)}, traction_face="zmax", steps=20, dt=0.01, newton_tol=1e-8, k=0.5, lam=100.0,
+        load_key="cube_p4_traction", load_scale=0.5),
     "static_fab": dict(
         elems=(2, 2, 2), P=4, lengths=(1.0, 1.0, 1.0), E=1.0e3, nu=0.3, rho=1.0,
         clamp={"xmin": (0, 1, 2)}, k=0.5, lam=100.0),
@@ -101,3 +112,14 @@ def random_vector(n, seed, scale=1.0):
 
 def random_uniform(n, seed, lo=-1.0, hi=1.0):
     return rng(seed).uniform(lo, hi, n)
+
+
+def batch_draws(w):
+    """Seeded per-problem draws of a batch workload: (side, P, E, nu) lists."""
+    g = rng(w["seed"])
+    n = w["count"]
+    side = g.integers(w["side"][0], w["side"][1] + 1, n)
+    P = g.choice(np.asarray(w["orders"]), n)
+    E = g.uniform(w["E"][0], w["E"][1], n)
+    nu = g.uniform(w["nu"][0], w["nu"][1], n)
+    return [int(v) for v in side], [int(v) for v in P], [float(v) for v in E], [float(v) for v in nu]
