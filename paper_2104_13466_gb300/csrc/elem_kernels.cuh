@@ -42,6 +42,10 @@ struct ElemTables {
   T CH[QH * QH];
   T CM[QH];
   T DM[QH];
+  // float32 path: the even/odd tables interleaved for packed (f32x2) FMAs,
+  // TEO[q][k] = {TE[q][k], TO[q][k]} (k < NO), ACH[q][m] = {AH[q][m], CH[q][m]}
+  alignas(8) T TEO[QH * NO * 2];
+  alignas(8) T ACH[QH * QH * 2];
 };
 
 // Per-mesh scalars of an element kernel (one problem of a batch, or the
@@ -99,6 +103,26 @@ __device__ __forceinline__ void from_canonical(T (&v)[n]) {
   if ((n - 2) % 2 == 1) v[(n - 1) / 2] = t[n - 2];
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (the 16-byte-aligned interior).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t lo = (a + 15) & ~uintptr_t(15), hi = (a + bytes) & ~uintptr_t(15);
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
+// Packed float32 multiply-add on a register pair: acc = t * v + acc, lane-wise.
+__device__ __forceinline__ void ffma2(float& ax, float& ay, float tx, float ty, float vx, float vy) {
+  asm("{\n\t.reg .b64 pa, pb, pc;\n\t"
+      "mov.b64 pa, {%2, %3};\n\t"
+      "mov.b64 pb, {%4, %5};\n\t"
+      "mov.b64 pc, {%0, %1};\n\t"
+      "fma.rn.f32x2 pc, pa, pb, pc;\n\t"
+      "mov.b64 {%0, %1}, pc;\n\t}"
+      : "+f"(ax), "+f"(ay)
+      : "f"(tx), "f"(ty), "f"(vx), "f"(vy));
+}
+
 // out[q] = sum_j B[q][j] in[j] (modes -> Gauss points)
 template <typename T, int P>
 __device__ __forceinline__ void eo_interp(const ElemTables<T, P>& tb, const T (&in)[P + 1], T (&out)[P + 2]) {
@@ -114,10 +138,17 @@ __device__ __forceinline__ void eo_interp(const ElemTables<T, P>& tb, const T (&
 #pragma unroll
   for (int q = 0; q < QH; ++q) {
     T S = T(0), D = T(0);
+    if constexpr (sizeof(T) == 4) {
 #pragma unroll
-    for (int k = 0; k < NE; ++k) S += tb.TE[q * NE + k] * e[k];
+      for (int k = 0; k < NO; ++k)
+        ffma2(S, D, tb.TEO[2 * (q * NO + k)], tb.TEO[2 * (q * NO + k) + 1], e[k], o[k]);
+      if (NE > NO) S += tb.TE[q * NE + NE - 1] * e[NE - 1];
+    } else {
 #pragma unroll
-    for (int k = 0; k < NO; ++k) D += tb.TO[q * NO + k] * o[k];
+      for (int k = 0; k < NE; ++k) S += tb.TE[q * NE + k] * e[k];
+#pragma unroll
+      for (int k = 0; k < NO; ++k) D += tb.TO[q * NO + k] * o[k];
+    }
     out[q] = S + D;
     out[Q - 1 - q] = S - D;
   }
@@ -141,19 +172,36 @@ __device__ __forceinline__ void eo_interp_t(const ElemTables<T, P>& tb, const T 
     dv[q] = in[q] - in[Q - 1 - q];
   }
   T ee[NE], oo[NO];
+  if constexpr (sizeof(T) == 4) {
 #pragma unroll
-  for (int k = 0; k < NE; ++k) {
-    T a = (Q % 2 == 1) ? tb.TEm[k] * in[QH] : T(0);
+    for (int k = 0; k < NO; ++k) {
+      T a = (Q % 2 == 1) ? tb.TEm[k] * in[QH] : T(0), c = T(0);
 #pragma unroll
-    for (int q = 0; q < QH; ++q) a += tb.TE[q * NE + k] * sv[q];
-    ee[k] = a;
-  }
+      for (int q = 0; q < QH; ++q) ffma2(a, c, tb.TEO[2 * (q * NO + k)], tb.TEO[2 * (q * NO + k) + 1], sv[q], dv[q]);
+      ee[k] = a;
+      oo[k] = c;
+    }
+    if (NE > NO) {
+      T a = (Q % 2 == 1) ? tb.TEm[NE - 1] * in[QH] : T(0);
 #pragma unroll
-  for (int k = 0; k < NO; ++k) {
-    T a = T(0);
+      for (int q = 0; q < QH; ++q) a += tb.TE[q * NE + NE - 1] * sv[q];
+      ee[NE - 1] = a;
+    }
+  } else {
 #pragma unroll
-    for (int q = 0; q < QH; ++q) a += tb.TO[q * NO + k] * dv[q];
-    oo[k] = a;
+    for (int k = 0; k < NE; ++k) {
+      T a = (Q % 2 == 1) ? tb.TEm[k] * in[QH] : T(0);
+#pragma unroll
+      for (int q = 0; q < QH; ++q) a += tb.TE[q * NE + k] * sv[q];
+      ee[k] = a;
+    }
+#pragma unroll
+    for (int k = 0; k < NO; ++k) {
+      T a = T(0);
+#pragma unroll
+      for (int q = 0; q < QH; ++q) a += tb.TO[q * NO + k] * dv[q];
+      oo[k] = a;
+    }
   }
   out[0] = ee[0] + oo[0];
   out[n - 1] = ee[0] - oo[0];
@@ -179,8 +227,12 @@ __device__ __forceinline__ void eo_deriv(const ElemTables<T, P>& tb, const T (&u
     T X = T(0), Y = (Q % 2 == 1) ? tb.CM[q] * u[QH] : T(0);
 #pragma unroll
     for (int m = 0; m < QH; ++m) {
-      X += tb.AH[q * QH + m] * du[m];
-      Y += tb.CH[q * QH + m] * su[m];
+      if constexpr (sizeof(T) == 4) {
+        ffma2(X, Y, tb.ACH[2 * (q * QH + m)], tb.ACH[2 * (q * QH + m) + 1], du[m], su[m]);
+      } else {
+        X += tb.AH[q * QH + m] * du[m];
+        Y += tb.CH[q * QH + m] * su[m];
+      }
     }
     out[q] = X + Y;
     out[Q - 1 - q] = X - Y;
@@ -209,8 +261,12 @@ __device__ __forceinline__ void eo_deriv_t(const ElemTables<T, P>& tb, const T (
     T X = T(0), Y = (Q % 2 == 1) ? tb.DM[m] * g[QH] : T(0);
 #pragma unroll
     for (int q = 0; q < QH; ++q) {
-      X += tb.CH[q * QH + m] * dg[q];
-      Y += tb.AH[q * QH + m] * sg[q];
+      if constexpr (sizeof(T) == 4) {
+        ffma2(Y, X, tb.ACH[2 * (q * QH + m)], tb.ACH[2 * (q * QH + m) + 1], sg[q], dg[q]);
+      } else {
+        X += tb.CH[q * QH + m] * dg[q];
+        Y += tb.AH[q * QH + m] * sg[q];
+      }
     }
     out[m] = X + Y;
     out[Q - 1 - m] = X - Y;
@@ -606,10 +662,17 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
                                              unsigned nparts, PcgScalars* __restrict__ scal, T* sm) {
   using G = Geo<P>;
   constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
+  constexpr int NT = G::NT;  // == blockDim.x: compile-time strides let the loops batch their loads
   if (scal && scal->status != 0) return;
+  if constexpr (STIFF) {
+    // start pulling the element's linearisation state into L2 now; the
+    // pointwise stage reads it after the gather and the forward stages
+    if (threadIdx.x == 0) prefetch_l2(st + (int64_t)e * kStateFields * Q3, sizeof(T) * kStateFields * Q3);
+  }
   T* X = sm + 3 * FQ;
   const ElemView<MeshParams<T>> view(m, P, e);
-  for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
+#pragma unroll
+  for (int idx = threadIdx.x; idx < 3 * n3; idx += NT) {
     bool cons;
     int so;
     const int64_t g = entry_index<P>(m, view, idx, &cons, &so);
@@ -628,7 +691,7 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
       for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= mfac;
     }
   }
-  for (int q = threadIdx.x; STIFF && q < Q3; q += blockDim.x) {
+  for (int q = threadIdx.x; STIFF && q < Q3; q += NT) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
     const int so = (qz * Q + qy) * XQ + qx;
     T H[3][3], dF[3][3];
@@ -668,7 +731,8 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
   __syncthreads();
   transpose_stages<T, P, STIFF>(tb, pairs, sm);
   T dotT = T(0);
-  for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
+#pragma unroll
+  for (int idx = threadIdx.x; idx < 3 * n3; idx += NT) {
     bool cons;
     int so;
     const int64_t g = entry_index<P>(m, view, idx, &cons, &so);

@@ -28,6 +28,16 @@ static ElemParams<T, P> make_params(const HostElemData& h, double b1) {
     p.tab.CM[i] = (T)h.CM[i];
     p.tab.DM[i] = (T)h.DM[i];
   }
+  for (int q = 0; q < E::QH; ++q) {
+    for (int k = 0; k < E::NO; ++k) {
+      p.tab.TEO[2 * (q * E::NO + k)] = (T)h.TE[q * E::NE + k];
+      p.tab.TEO[2 * (q * E::NO + k) + 1] = (T)h.TO[q * E::NO + k];
+    }
+    for (int m = 0; m < E::QH; ++m) {
+      p.tab.ACH[2 * (q * E::QH + m)] = (T)h.AH[q * E::QH + m];
+      p.tab.ACH[2 * (q * E::QH + m) + 1] = (T)h.CH[q * E::QH + m];
+    }
+  }
   p.pairs = h.pairs;
   for (int d = 0; d < 3; ++d) {
     p.s[d] = (T)h.s[d];
