@@ -10,19 +10,23 @@ import numpy as np
 import scipy.sparse as sp
 
 from .element import RefElement
-from .quadrature import gauss_legendre
 
 _FACE_AXIS = {"xmin": (0, 0), "xmax": (0, 1), "ymin": (1, 0), "ymax": (1, 1),
               "zmin": (2, 0), "zmax": (2, 1)}
 
 
 class Discretization:
-    def __init__(self, mesh, basis, mu, lam, rho=1.0, Q=None, chunk=512):
+    def __init__(self, mesh, basis, mu, lam, rho=1.0, Q=None, chunk=512, mass_rule="gauss"):
+        """mass_rule "gll": the mass matrix (only) is integrated at the P + 1
+        Gauss-Lobatto-Legendre points, which for the Lagrange basis on those
+        points gives the diagonal (lumped) mass of the paper's explicit Lagrange
+        runs; stiffness and loads keep the Gauss rule."""
         if basis.P != mesh.P:
             raise ValueError("basis order must match mesh order")
         self.mesh, self.basis = mesh, basis
         self.mu, self.lam, self.rho = float(mu), float(lam), float(rho)
         self.ref = RefElement(basis, mesh.h, Q)
+        self.mref = RefElement(basis, mesh.h, rule="gll") if mass_rule == "gll" else self.ref
         self.edofs = mesh.element_dofs()
         self.mask = mesh.constrained()
         self.chunk = chunk
@@ -50,7 +54,7 @@ class Discretization:
     def mass_apply(self, x):
         out = np.zeros(self.mesh.ndof)
         for s in self._chunks():
-            out += self.scatter(self.ref.mass_action(self.gather(x, s), self.rho), s)
+            out += self.scatter(self.mref.mass_action(self.gather(x, s), self.rho), s)
         return out
 
     def tangent_apply(self, u, x, b1=0.0):
@@ -60,7 +64,7 @@ class Discretization:
             Ue, Xe = self.gather(u, s), self.gather(x, s)
             Ye = self.ref.tangent_action(Ue, Xe, self.mu, self.lam)
             if b1 != 0.0:
-                Ye = Ye + b1 * self.ref.mass_action(Xe, self.rho)
+                Ye = Ye + b1 * self.mref.mass_action(Xe, self.rho)
             out += self.scatter(Ye, s)
         return out
 
@@ -99,7 +103,7 @@ class Discretization:
 
     def mass_diagonal(self):
         """diag(M): rho sum_q w_q N_m(q)^2 summed over elements."""
-        De = self.rho * (self.ref.w @ (self.ref.N * self.ref.N))
+        De = self.rho * (self.mref.w @ (self.mref.N * self.mref.N))
         out = np.zeros(self.mesh.ndof)
         for s in self._chunks():
             E = s.stop - s.start
@@ -132,7 +136,7 @@ class Discretization:
         return K.tocsr()
 
     def mass_matrix(self):
-        Me = self.ref.mass_matrix(self.rho)
+        Me = self.mref.mass_matrix(self.rho)
         rows, cols, vals = [], [], []
         for e in range(self.mesh.nelem):
             idx = self.edofs[e].ravel()
@@ -172,7 +176,7 @@ class Discretization:
         axis, side = _FACE_AXIS[face]
         tang = [d for d in range(3) if d != axis]
         Q = self.ref.Q
-        xq, wq = gauss_legendre(Q)
+        xq, wq = self.ref.xq, self.ref.wq1                            # the element's own rule
         B, _ = basis.tables(xq)                                       # (Q, n)
         Bend, _ = basis.tables(np.array([-1.0 if side == 0 else 1.0]))  # (1, n)
         n = mesh.n

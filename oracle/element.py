@@ -20,16 +20,26 @@ Operators (vectorised over elements, arrays U[e, c, m]):
 import numpy as np
 
 from . import material
-from .quadrature import gauss_legendre
+from .quadrature import gauss_legendre, gauss_lobatto_legendre_rule
 
 
 class RefElement:
-    def __init__(self, basis, h, Q=None):
+    """rule "gauss": Q (default P + 2) Gauss-Legendre points per direction;
+    rule "gll": the P + 1 Gauss-Lobatto-Legendre points (collocation
+    integration at the nodes of the Lagrange basis, Sec. 2: with that basis
+    the mass matrix is diagonal)."""
+
+    def __init__(self, basis, h, Q=None, rule="gauss"):
         self.basis = basis
         self.P = basis.P
         self.n = basis.P + 1
-        self.Q = Q or (basis.P + 2)
-        xq, wq = gauss_legendre(self.Q)
+        self.rule = rule
+        if rule == "gll":
+            self.Q = self.n
+            xq, wq = gauss_lobatto_legendre_rule(self.P)
+        else:
+            self.Q = Q or (basis.P + 2)
+            xq, wq = gauss_legendre(self.Q)
         self.xq, self.wq1 = xq, wq
         B, D = basis.tables(xq)
         self.B, self.D = B, D

@@ -68,3 +68,16 @@ def gauss_lobatto_legendre(P):
         return np.array([-1.0, 1.0])
     inner, _ = gauss_jacobi(P - 1, 1.0, 1.0)
     return np.concatenate(([-1.0], inner, [1.0]))
+
+
+def gauss_lobatto_legendre_rule(P):
+    """P + 1 point Gauss-Lobatto-Legendre rule (nodes, weights): the nodes of
+    ``gauss_lobatto_legendre`` with the textbook weights
+    w_i = 2 / (P (P + 1) L_P(x_i)^2), L_P the Legendre polynomial (three-term
+    recurrence).  Exact for polynomials of degree 2P - 1."""
+    x = gauss_lobatto_legendre(P)
+    L0, L1 = np.ones_like(x), x.copy()
+    for k in range(1, P):
+        L0, L1 = L1, ((2 * k + 1) * x * L1 - k * L0) / (k + 1)
+    LP = L1 if P >= 1 else L0
+    return x, 2.0 / (P * (P + 1) * LP * LP)

@@ -16,8 +16,8 @@ MU, LAM = lame(1000.0, 0.3)
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def _run_fabricated(P, kind="sdme_m", T=0.25, N=800):
-    d = Discretization(BoxMesh(2, 2, 2, P).clamp("xmin"), Basis1D(P, kind), MU, LAM)
+def _run_fabricated(P, kind="sdme_m", T=0.25, N=800, mass_rule="gauss"):
+    d = Discretization(BoxMesh(2, 2, 2, P).clamp("xmin"), Basis1D(P, kind), MU, LAM, mass_rule=mass_rule)
     fld = manufactured.sine_field()
     dt = T / N
     u = np.zeros(d.mesh.ndof)
@@ -40,6 +40,40 @@ def test_explicit_fabricated_matches_paper_table(P):
     # quadrature and norm are unstated: order-of-magnitude pin
     for have, want in zip(err, row[1:]):
         assert want / 3.0 < have < want * 3.0, (err, row)
+
+
+@pytest.mark.parametrize("P", [2, 4])
+def test_explicit_lumped_lagrange_matches_paper_table(P):
+    # nodal basis with its mass integrated at its own GLL nodes (diagonal
+    # mass, no solve per step); stiffness and loads with the Gauss rule.
+    # (Integrating the stiffness and loads at the GLL nodes as well gives
+    # errors 10x (P = 2) to 20x (P = 4) larger than the paper's table.)
+    with open(os.path.join(GOLDEN, "explicit_fab_lagrange_l2.json")) as fh:
+        g = json.load(fh)
+    row = [r for r in g["rows"] if r[0] == P][0]
+    err = _run_fabricated(P, kind="nodal", T=g["T"], N=g["steps"], mass_rule="gll")
+    for have, want in zip(err, row[1:]):
+        assert want / 3.0 < have < want * 3.0, (err, row)
+
+
+def test_gll_collocation_mass_is_diagonal():
+    P = 3
+    d = Discretization(BoxMesh(2, 1, 1, P), Basis1D(P, "nodal"), MU, LAM, rho=2.0, mass_rule="gll")
+    M = d.mass_matrix().toarray()
+    off = M - np.diag(np.diag(M))
+    assert np.abs(off).max() < 1e-13 * np.abs(M).max()
+    # diagonal = rho detJ w_i w_j w_k summed over the elements sharing the node
+    from oracle.quadrature import gauss_lobatto_legendre_rule
+    _, w = gauss_lobatto_legendre_rule(P)
+    h = d.mesh.h
+    m1 = np.zeros(d.mesh.N[0])
+    for e in range(2):
+        m1[e * P:e * P + P + 1] += w * h[0] / 2
+    my, mz = w * h[1] / 2, w * h[2] / 2
+    want = 2.0 * np.einsum("k,j,i->kji", mz, my, m1).ravel()
+    assert np.allclose(np.diag(M)[:want.size], want, rtol=1e-13)
+    # the lumped mass still integrates the constant exactly: total mass
+    assert abs(np.diag(M)[:want.size].sum() - 2.0 * np.prod(d.mesh.lengths)) < 1e-12
 
 
 def _stable_dt(d):

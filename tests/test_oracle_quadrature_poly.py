@@ -74,3 +74,23 @@ def test_lagrange_collocation_and_partition():
     for a in range(7):
         fd = (lagrange(nodes, a, x + h) - lagrange(nodes, a, x - h)) / (2 * h)
         assert np.allclose(lagrange_deriv(nodes, a, x), fd, atol=1e-6)
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 5, 8])
+def test_gll_rule_exactness(P):
+    from oracle.quadrature import gauss_lobatto_legendre_rule
+    x, w = gauss_lobatto_legendre_rule(P)
+    for k in range(2 * P):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs(np.sum(w * x ** k) - exact) < 1e-13
+    if P >= 2:
+        # degree 2P is not integrated exactly (P + 1 point Lobatto rule)
+        assert abs(np.sum(w * x ** (2 * P)) - 2.0 / (2 * P + 1)) > 1e-6
+
+
+def test_gll_rule_textbook_values():
+    from oracle.quadrature import gauss_lobatto_legendre_rule
+    x, w = gauss_lobatto_legendre_rule(2)
+    assert np.allclose(x, [-1, 0, 1]) and np.allclose(w, [1 / 3, 4 / 3, 1 / 3])
+    x, w = gauss_lobatto_legendre_rule(3)
+    assert np.allclose(x, [-1, -1 / np.sqrt(5), 1 / np.sqrt(5), 1]) and np.allclose(w, [1 / 6, 5 / 6, 5 / 6, 1 / 6])
