@@ -683,7 +683,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--basis", default="sdme_h", choices=["nodal", "modal", "sdme_m", "sdme_k", "sdme_h"])
+    ap.add_argument("--basis", default="sdme_h",
+                    choices=["nodal", "modal", "sdme_m", "sdme_k", "sdme_h", "nodal_lumped"])
     ap.add_argument("--workload", default="beam_p8")
     ap.add_argument("--mixed-rtol", type=float, default=1e-4)
     ap.add_argument("--pcg-maxit", type=int, default=20000)

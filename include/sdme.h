@@ -56,7 +56,12 @@ typedef enum {
   SDME_MODAL = 1,    /* Jacobi modal ST basis, eq. BasePadrao1D */
   SDME_SDME_M = 2,   /* SD internal modes + ME vertex modes, L2 norm (eq. alphaMassa) */
   SDME_SDME_K = 3,   /* SD + ME, energy norm (eq. alphaRigidez) */
-  SDME_SDME_H = 4    /* SD + ME, Helmholtz norm K + lambda M (eq. alphaKN) */
+  SDME_SDME_H = 4,   /* SD + ME, Helmholtz norm K + lambda M (eq. alphaKN) */
+  SDME_NODAL_LUMPED = 5 /* the nodal basis with its mass matrix integrated at its own
+                           Gauss-Lobatto-Legendre nodes: diagonal (lumped) mass, the
+                           diagonal-mass Lagrange variant of Sec. 5.2.1; stiffness and
+                           loads as for SDME_NODAL.  Mass solves are divisions (no PCG);
+                           operators with a mass term (b1 != 0) are SDME_EUNSUPPORTED. */
 } sdme_basis_kind;
 
 typedef enum {

@@ -19,8 +19,9 @@ LIB_PATH = os.path.join(_HERE, "libsdme.so")
 # status codes (sdme_status)
 OK, EINVAL, ENOMEM, ECUDA, PCG_MAXIT, NEWTON_DIVERGED, NONPOSITIVE_J, NAN, TIMEOUT, EUNSUPPORTED = range(10)
 # basis kinds (sdme_basis_kind)
-NODAL, MODAL, SDME_M, SDME_K, SDME_H = range(5)
-KIND_NAMES = {"nodal": NODAL, "modal": MODAL, "sdme_m": SDME_M, "sdme_k": SDME_K, "sdme_h": SDME_H}
+NODAL, MODAL, SDME_M, SDME_K, SDME_H, NODAL_LUMPED = range(6)
+KIND_NAMES = {"nodal": NODAL, "modal": MODAL, "sdme_m": SDME_M, "sdme_k": SDME_K, "sdme_h": SDME_H,
+              "nodal_lumped": NODAL_LUMPED}
 # precisions (sdme_precision)
 FP64, MIXED_FP32 = 0, 1
 # faces

@@ -67,6 +67,8 @@ struct sdme_ctx {
   float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr, *x32 = nullptr;
   // Newton work vectors
   double *un = nullptr, *ahat = nullptr, *mhat = nullptr, *y = nullptr, *psi = nullptr, *du = nullptr;
+  // lumped (diagonal) mass of SDME_NODAL_LUMPED contexts, else null
+  double* mlump = nullptr;
   // pinned host mirrors
   PcgScalars* scal_h = nullptr;
   double* dscal_h = nullptr;
@@ -109,13 +111,15 @@ cudaError_t dispatch_P(int P, F&& f) {
 }
 
 sdme_status check_basis(const sdme_basis_desc* b) {
-  if (!b || b->P < 1 || b->P > kMaxP || b->kind < SDME_NODAL || b->kind > SDME_SDME_H) return SDME_EINVAL;
+  if (!b || b->P < 1 || b->P > kMaxP || b->kind < SDME_NODAL || b->kind > SDME_NODAL_LUMPED) return SDME_EINVAL;
   if (b->kind >= SDME_SDME_M && (b->k < 0.0 || b->k > 1.0)) return SDME_EINVAL;
   return SDME_OK;
 }
 
+// SDME_NODAL_LUMPED uses the nodal basis (only its mass treatment differs)
 bool build_basis(const sdme_basis_desc* b, Basis1D& out) {
-  return out.build(b->P, (int)b->kind, b->k, b->lambda, b->start_nodal != 0, b->jacobi_alpha, b->jacobi_beta);
+  const int kind = b->kind == SDME_NODAL_LUMPED ? (int)SDME_NODAL : (int)b->kind;
+  return out.build(b->P, kind, b->k, b->lambda, b->start_nodal != 0, b->jacobi_alpha, b->jacobi_beta);
 }
 
 template <typename T>
@@ -331,6 +335,49 @@ sdme_status pcg_dispatch(sdme_ctx* ctx, double b1, const double* b, double* x, d
                                   ctx->d64, ctx->x64);
 }
 
+// M x = b on the free DOFs (x = 0 on constrained ones): Jacobi-PCG on the
+// consistent mass, or a division by the lumped mass of SDME_NODAL_LUMPED.
+sdme_status mass_solve_core(sdme_ctx* ctx, const double* b, double* x, double rtol, int maxit, int* iters,
+                            double* rel) {
+  if (ctx->mlump) {
+    k_lumped_solve<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, ctx->mlump, b, x);
+    SDME_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 1;
+    if (iters) *iters = 0;
+    if (rel) *rel = 0.0;
+    return SDME_OK;
+  }
+  return pcg_dispatch(ctx, 1.0, b, x, rtol, maxit, iters, rel, true);
+}
+
+// Lumped mass of SDME_NODAL_LUMPED: rho detJ w_p w_q w_r (GLL weights) per
+// element node, summed over the elements sharing the node; the same for the
+// three components.
+sdme_status build_lumped_mass(sdme_ctx* ctx) {
+  const HostElemData& h = ctx->h;
+  const int P = h.P, n = P + 1;
+  std::vector<double> x(n), w(n);
+  gauss_lobatto_legendre(P, x.data());
+  gauss_lobatto_weights(P, x.data(), w.data());
+  std::vector<double> m(ctx->ndof, 0.0);
+  const double f = h.rho * h.detJ;
+  for (int ez = 0; ez < h.ne[2]; ++ez)
+    for (int ey = 0; ey < h.ne[1]; ++ey)
+      for (int ex = 0; ex < h.ne[0]; ++ex)
+        for (int r = 0; r < n; ++r)
+          for (int q = 0; q < n; ++q)
+            for (int p = 0; p < n; ++p) {
+              const int64_t node = ((int64_t)(ez * P + r) * h.N[1] + (ey * P + q)) * h.N[0] + (ex * P + p);
+              m[node] += f * w[p] * w[q] * w[r];
+            }
+  for (int c = 1; c < 3; ++c)
+    for (int64_t i = 0; i < h.Nn; ++i) m[c * h.Nn + i] = m[i];
+  SDME_CUDA(dalloc(&ctx->mlump, ctx->ndof));
+  SDME_CUDA(cudaMemcpyAsync(ctx->mlump, m.data(), sizeof(double) * ctx->ndof, cudaMemcpyHostToDevice, ctx->stream));
+  SDME_CUDA(cudaStreamSynchronize(ctx->stream));
+  return SDME_OK;
+}
+
 // x . y (float64, deterministic), synchronises
 sdme_status dot_host(sdme_ctx* ctx, const double* x, const double* y, double* out) {
   k_dot<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, x, y, ctx->partial, ctx->dcount, ctx->dscal);
@@ -345,7 +392,7 @@ sdme_status dot_host(sdme_ctx* ctx, const double* x, const double* y, double* ou
 void free_all(sdme_ctx* ctx) {
   void* dev[] = {ctx->st64, ctx->st32, ctx->err, ctx->scal, ctx->partial, ctx->dscal, ctx->dcount,
                  ctx->r64, ctx->p64, ctx->q64, ctx->d64, ctx->x64, ctx->r32, ctx->p32, ctx->q32, ctx->d32,
-                 ctx->x32, ctx->un, ctx->ahat, ctx->mhat, ctx->y, ctx->psi, ctx->du};
+                 ctx->x32, ctx->un, ctx->ahat, ctx->mhat, ctx->y, ctx->psi, ctx->du, ctx->mlump};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (ctx->scal_h) cudaFreeHost(ctx->scal_h);
@@ -408,7 +455,7 @@ sdme_status adjoint_kernel_step(sdme_tape* tp, const double* u, const double* g,
   double* Kz = tp->v[7];
   int its = 0;
   double rel = 0.0;
-  SDME_TRY(pcg_dispatch(ctx, 1.0, g, z, tp->rtol, tp->maxit, &its, &rel, true));
+  SDME_TRY(mass_solve_core(ctx, g, z, tp->rtol, tp->maxit, &its, &rel));
   double pm = 0.0, pl = 0.0;
   SDME_TRY(sdme_internal_force_vjp(ctx, u, z, Kz, &pm, &pl));
   gth[0] -= c * pm;
@@ -581,6 +628,7 @@ sdme_status sdme_create(sdme_ctx** out, const sdme_mesh_desc* mesh, const sdme_m
          cudaMemsetAsync(ctx->dcount, 0, 8 * sizeof(unsigned int), ctx->stream) == cudaSuccess &&
          cudaStreamSynchronize(ctx->stream) == cudaSuccess;
   }
+  if (ok && basis->kind == SDME_NODAL_LUMPED) ok = build_lumped_mass(ctx) == SDME_OK;
   if (!ok) {
     cudaGetLastError();
     free_all(ctx);
@@ -649,6 +697,12 @@ sdme_status sdme_internal_force_vjp(sdme_ctx* ctx, const double* u_dev, const do
 
 sdme_status sdme_mass_apply(sdme_ctx* ctx, const double* x_dev, double* y_dev) {
   if (!ctx || !x_dev || !y_dev) return SDME_EINVAL;
+  if (ctx->mlump) {
+    k_diag_mul<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, ctx->mlump, x_dev, y_dev);
+    SDME_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 1;
+    return SDME_OK;
+  }
   SDME_CUDA(cudaMemsetAsync(y_dev, 0, sizeof(double) * ctx->ndof, ctx->stream));
   SDME_CUDA(dispatch_P(ctx->h.P, [&](auto Pc) {
     return launch_mass<decltype(Pc)::value>(ctx->h, x_dev, y_dev, ctx->stream);
@@ -659,6 +713,7 @@ sdme_status sdme_mass_apply(sdme_ctx* ctx, const double* x_dev, double* y_dev) {
 
 sdme_status sdme_tangent_apply(sdme_ctx* ctx, const double* u_dev, double b1, const double* x_dev, double* y_dev) {
   if (!ctx || !u_dev || !x_dev || !y_dev) return SDME_EINVAL;
+  if (ctx->mlump && b1 != 0.0) return SDME_EUNSUPPORTED;
   SDME_TRY(residual_launch(ctx, 0.0, u_dev, ctx->y));
   SDME_TRY(sync_and_check(ctx));
   k_mask_init<double><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, x_dev, y_dev);
@@ -670,6 +725,7 @@ sdme_status sdme_tangent_apply(sdme_ctx* ctx, const double* u_dev, double b1, co
 
 sdme_status sdme_diagonal(sdme_ctx* ctx, const double* u_dev, double b1, double* d_dev) {
   if (!ctx || !u_dev || !d_dev) return SDME_EINVAL;
+  if (ctx->mlump && b1 != 0.0) return SDME_EUNSUPPORTED;
   SDME_TRY(residual_launch(ctx, 0.0, u_dev, ctx->y));
   SDME_TRY(sync_and_check(ctx));
   return diag_launch<double>(ctx, b1, d_dev, 0);
@@ -678,6 +734,7 @@ sdme_status sdme_diagonal(sdme_ctx* ctx, const double* u_dev, double b1, double*
 sdme_status sdme_pcg_solve(sdme_ctx* ctx, const double* u_dev, double b1, const double* b_dev, double* x_dev,
                            double rtol, int maxit, int* iters, double* final_rel) {
   if (!ctx || !u_dev || !b_dev || !x_dev || maxit < 1 || !(rtol >= 0.0)) return SDME_EINVAL;
+  if (ctx->mlump && b1 != 0.0) return SDME_EUNSUPPORTED;
   SDME_TRY(residual_launch(ctx, 0.0, u_dev, ctx->y));
   SDME_TRY(sync_and_check(ctx));
   return pcg_dispatch(ctx, b1, b_dev, x_dev, rtol, maxit, iters, final_rel);
@@ -718,6 +775,7 @@ sdme_status sdme_traction_load(sdme_ctx* ctx, int face, const double t[3], doubl
 sdme_status sdme_implicit_newmark_step(sdme_ctx* ctx, sdme_state* state, double dt, const double* P_next_dev,
                                        const sdme_newton_opts* opts, sdme_step_stats* stats) {
   if (!ctx || !state || !state->u || !state->v || !state->a || !P_next_dev || !(dt > 0.0)) return SDME_EINVAL;
+  if (ctx->mlump) return SDME_EUNSUPPORTED;
   sdme_newton_opts o{0.25, 0.5, 1e-8, 30, 1e-10, 1e-4, 20000};
   if (opts) o = *opts;
   if (!(o.beta > 0.0) || o.max_newton < 0 || o.pcg_maxit < 1) return SDME_EINVAL;
@@ -794,7 +852,7 @@ sdme_status sdme_explicit_start(sdme_ctx* ctx, sdme_explicit_state* st, double d
   SDME_TRY(sync_and_check(ctx));
   int its = 0;
   double rel = 0.0;
-  sdme_status ps = pcg_dispatch(ctx, 1.0, ctx->psi, st->a, rtol, maxit, &its, &rel, true);
+  sdme_status ps = mass_solve_core(ctx, ctx->psi, st->a, rtol, maxit, &its, &rel);
   if (ps != SDME_OK) return ps;
   k_cd_start<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, st->u, v0_dev, st->a, dt, st->u_prev);
   SDME_CUDA(cudaGetLastError());
@@ -807,6 +865,18 @@ sdme_status sdme_explicit_step(sdme_ctx* ctx, sdme_explicit_state* st, double dt
                                int maxit, int* pcg_iters) {
   if (!ctx || !st || !st->u || !st->u_prev || !st->a || !Pn_dev || !(dt > 0.0) || maxit < 1) return SDME_EINVAL;
   SDME_TRY(residual_launch(ctx, 0.0, st->u, ctx->y, false));
+  if (ctx->mlump) {
+    // diagonal mass: acceleration and update in one pass, no solve
+    k_cd_lumped<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, st->u, Pn_dev, ctx->y, ctx->mlump, dt * dt,
+                                                             st->a, st->u_prev);
+    SDME_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 1;
+    if (pcg_iters) *pcg_iters = 0;
+    double* t = st->u;
+    st->u = st->u_prev;
+    st->u_prev = t;
+    return sync_and_check(ctx);
+  }
   k_residual_combine<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, Pn_dev, nullptr, ctx->y, ctx->psi,
                                                                   ctx->partial, ctx->dcount, ctx->dscal);
   SDME_CUDA(cudaGetLastError());
@@ -877,7 +947,7 @@ sdme_status sdme_estimate_dt_crit(sdme_ctx* ctx, const double* u_dev, int iters,
     lam = xKx / xMx;
     int its = 0;
     double rel = 0.0;
-    sdme_status ps = pcg_dispatch(ctx, 1.0, Kx, x, 1e-6, 2000, &its, &rel, true);
+    sdme_status ps = mass_solve_core(ctx, Kx, x, 1e-6, 2000, &its, &rel);
     if (ps != SDME_OK && ps != SDME_PCG_MAXIT) return ps;
     ctx->kernel_launches += 3;
   }
@@ -900,7 +970,7 @@ sdme_status sdme_body_load(sdme_ctx* ctx, const double* fq_dev, double* f_dev) {
 sdme_status sdme_mass_solve(sdme_ctx* ctx, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters,
                             double* final_rel) {
   if (!ctx || !b_dev || !x_dev || maxit < 1 || !(rtol >= 0.0)) return SDME_EINVAL;
-  return pcg_dispatch(ctx, 1.0, b_dev, x_dev, rtol, maxit, iters, final_rel, true);
+  return mass_solve_core(ctx, b_dev, x_dev, rtol, maxit, iters, final_rel);
 }
 
 sdme_status sdme_gauss_points(const sdme_ctx* ctx, double* xq, double* wq) {

@@ -218,6 +218,18 @@ void lagrange_eval(int n, const double* xn, double x, double* val, double* der) 
   }
 }
 
+void gauss_lobatto_weights(int P, const double* x, double* w) {
+  for (int i = 0; i <= P; ++i) {
+    double l0 = 1.0, l1 = x[i];
+    for (int k = 1; k < P; ++k) {
+      const double l2 = ((2 * k + 1) * x[i] * l1 - k * l0) / (k + 1);
+      l0 = l1;
+      l1 = l2;
+    }
+    w[i] = 2.0 / (P * (P + 1) * l1 * l1);
+  }
+}
+
 bool Basis1D::build(int P_, int kind_, double k, double lam, bool start_nodal, double ja, double jb) {
   if (P_ < 1 || P_ > kMaxP) return false;
   P = P_;

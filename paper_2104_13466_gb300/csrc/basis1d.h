@@ -8,6 +8,9 @@ constexpr int kMaxP = 8;
 
 void gauss_legendre(int Q, double* x, double* w);
 void gauss_lobatto_legendre(int P, double* x);
+// Weights of the P + 1 point Gauss-Lobatto-Legendre rule at the nodes x:
+// w_i = 2 / (P (P + 1) L_P(x_i)^2).
+void gauss_lobatto_weights(int P, const double* x, double* w);
 void lagrange_eval(int n, const double* xn, double x, double* val, double* der);
 // DQ[q*Q + m] = derivative of the m-th Lagrange polynomial through the Q
 // points xq, evaluated at xq[q] (exact derivative of degree < Q polynomials

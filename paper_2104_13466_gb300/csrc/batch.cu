@@ -388,7 +388,8 @@ sdme_status sdme_batch_create(sdme_batch** out, const sdme_problem* probs, int n
   if (!out || !probs || nprob < 1 || !basis) return SDME_EINVAL;
   *out = nullptr;
   if (prec != SDME_FP64 && prec != SDME_MIXED_FP32) return SDME_EINVAL;
-  if (basis->kind < SDME_NODAL || basis->kind > SDME_SDME_H) return SDME_EINVAL;
+  if (basis->kind < SDME_NODAL || basis->kind > SDME_NODAL_LUMPED) return SDME_EINVAL;
+  if (basis->kind == SDME_NODAL_LUMPED) return SDME_EUNSUPPORTED;  // the batched step uses the consistent mass
   if (basis->kind >= SDME_SDME_M && (basis->k < 0.0 || basis->k > 1.0)) return SDME_EINVAL;
   for (int i = 0; i < nprob; ++i) {
     const sdme_problem& d = probs[i];

@@ -380,4 +380,44 @@ static __global__ void __launch_bounds__(kVecThreads) k_adj_start(MeshInfo mi, c
   }
 }
 
+
+// y = m x entry-wise (a lumped mass applied; no Dirichlet treatment).
+static __global__ void __launch_bounds__(kVecThreads) k_diag_mul(int64_t n, const double* __restrict__ m,
+                                                                 const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    y[g] = m[g] * x[g];
+}
+
+// x = b / m on free DOFs, 0 on constrained ones (a lumped mass solved).
+static __global__ void __launch_bounds__(kVecThreads) k_lumped_solve(MeshInfo mi, const double* __restrict__ m,
+                                                                     const double* __restrict__ b,
+                                                                     double* __restrict__ x) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
+       g += (int64_t)gridDim.x * blockDim.x)
+    x[g] = dof_constrained(mi, g) ? 0.0 : b[g] / m[g];
+}
+
+// One central-difference step with a lumped mass (Sec. 4.1, eq. Motion_explicit2):
+// a = (P - R) / m and u_prev <- 2 u - u_prev + dt^2 a on free DOFs; a = 0 and
+// u_prev <- u on constrained ones.
+static __global__ void __launch_bounds__(kVecThreads) k_cd_lumped(MeshInfo mi, const double* __restrict__ u,
+                                                                  const double* __restrict__ Pl,
+                                                                  const double* __restrict__ R,
+                                                                  const double* __restrict__ m, double dt2,
+                                                                  double* __restrict__ a,
+                                                                  double* __restrict__ u_prev) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const double un = u[g];
+    if (dof_constrained(mi, g)) {
+      a[g] = 0.0;
+      u_prev[g] = un;
+    } else {
+      const double ag = (Pl[g] - R[g]) / m[g];
+      a[g] = ag;
+      u_prev[g] = 2.0 * un - u_prev[g] + dt2 * ag;
+    }
+  }
+}
+
 }  // namespace sdme

@@ -157,3 +157,65 @@ def test_body_load_and_l2_projection():
     x = torch.zeros_like(f)
     its, rel = ctx.mass_solve(f, x, rtol=1e-13)
     assert _rel(_host(x), d.l2_project(func)) < 1e-10
+
+
+def _pair_lumped(P, clamp=None, elems=(2, 2, 2), rho=1.0):
+    import paper_2104_13466_gb300 as s
+    clamp = {"xmin": (0, 1, 2)} if clamp is None else clamp
+    ctx = s.Context(elems, (1.0, 1.0, 1.0), clamp, MU, LAM, rho, P, "nodal_lumped")
+    mesh = BoxMesh(*elems, P)
+    for f, c in clamp.items():
+        mesh.clamp(f, c)
+    return ctx, Discretization(mesh, Basis1D(P, "nodal"), MU, LAM, rho, mass_rule="gll")
+
+
+@pytest.mark.parametrize("P", [1, 2, 4, 6])
+def test_lumped_mass_apply_and_solve(P):
+    ctx, d = _pair_lumped(P, rho=1.7)
+    x = np.random.default_rng(P).standard_normal(d.mesh.ndof)
+    y = torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda")
+    ctx.mass_apply(_dev(x), y)
+    assert _rel(_host(y), d.mass_apply(x)) < 1e-13
+    z = torch.zeros_like(y)
+    its, _ = ctx.mass_solve(y, z)
+    assert its == 0
+    want = np.where(d.mask, 0.0, x)
+    assert _rel(_host(z), want) < 1e-13
+
+
+@pytest.mark.parametrize("P", [2, 3, 5])
+def test_lumped_explicit_steps_match_oracle(P):
+    ctx, d = _pair_lumped(P)
+    (u, up, a), (ug, upg, ag), its = _fabricated_run(ctx, d, 8, 2e-4, 1e-12)
+    assert _rel(ug, u) < 1e-10 and _rel(upg, up) < 1e-10
+    # a = (P - R) / m: the fabricated load nearly balances the internal force,
+    # so a carries the cancellation |P| / |P - R| (~1e3 here) on top of round-off
+    assert _rel(ag, a) < 1e-8
+    assert all(i == 0 for i in its)
+
+
+def test_lumped_energy_and_dt_crit():
+    clamp = {f: (0, 1, 2) for f in ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")}
+    ctx, d = _pair_lumped(3, clamp=clamp)
+    rng = np.random.default_rng(8)
+    v = rng.standard_normal(d.mesh.ndof)
+    ke, _ = ctx.energy(v=_dev(v))
+    assert abs(ke - d.kinetic_energy(v)) < 1e-12 * abs(d.kinetic_energy(v))
+    dt_gpu, lam_gpu = ctx.estimate_dt_crit(_dev(np.zeros(d.mesh.ndof)), iters=200)
+    free = ~d.mask
+    K = d.tangent_matrix(np.zeros(d.mesh.ndof), masked=False).toarray()[np.ix_(free, free)]
+    M = d.mass_matrix().toarray()[np.ix_(free, free)]
+    lmax = sla.eigh(K, M, eigvals_only=True)[-1]
+    assert 0.9 * lmax < lam_gpu <= lmax * (1 + 1e-9)
+
+
+def test_lumped_rejects_mass_coupled_operators():
+    import paper_2104_13466_gb300 as s
+    ctx, d = _pair_lumped(2)
+    z = torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda")
+    with pytest.raises(s.SdmeError) as ei:
+        ctx.tangent_apply(z, 1.0, z, z.clone())
+    assert ei.value.status == s.EUNSUPPORTED
+    y = torch.zeros_like(z)
+    ctx.tangent_apply(z, 0.0, _dev(np.ones(ctx.ndof)), y)   # the stiffness alone is available
+    assert _rel(_host(y), d.effective_apply(np.zeros(d.mesh.ndof), np.ones(d.mesh.ndof))) < 1e-10
