@@ -223,6 +223,20 @@ sdme_status sdme_pcg_solve(sdme_ctx* ctx, const double* u_dev, double b1, const 
 sdme_status sdme_traction_load(sdme_ctx* ctx, int face, const double t[3], double* f_dev);
 
 /*
+ * Static equilibrium R(u) = P by Newton-Raphson without inertia (the static
+ * problem of Sec. 5.1): psi = P - R(u), K_T(u) du = psi by Jacobi-PCG (rtol
+ * pcg_rtol in FP64, mixed_rtol in MIXED_FP32), u += du, until
+ * ||psi|| <= newton_tol max(||psi_0||, 1e-14 ||P||) or max_newton
+ * iterations.  u_dev: initial guess in, solution out (constrained entries
+ * are kept).  opts may be NULL (tol 1e-8, 50 iterations, pcg_rtol 1e-12);
+ * beta and gamma are ignored.  Returns SDME_OK when converged,
+ * SDME_NEWTON_DIVERGED otherwise, or the inner solver's failure.
+ * Synchronises.
+ */
+sdme_status sdme_static_solve(sdme_ctx* ctx, double* u_dev, const double* P_dev, const sdme_newton_opts* opts,
+                              sdme_step_stats* stats);
+
+/*
  * One implicit Newmark step t_n -> t_{n+1} solved by Newton-Raphson with
  * Jacobi-PCG linear solves (Sec. 4.2, eqs. Eq:residual, NR_explicit):
  *   psi = P_{n+1} - R(u^k) - M a(u^k),  a(u) = b1 (u - u_n) - b2 v_n - b3 a_n,

@@ -470,6 +470,60 @@ sdme_status adjoint_kernel_step(sdme_tape* tp, const double* u, const double* g,
 
 }  // namespace
 
+// Newton-Raphson on psi(u) = P + mhat - (R(u) + b1 M u) = 0 (mhat may be
+// null: no inertia), Jacobi-PCG inner solves on (b1 M + K_T(u)).  Updates u
+// in place; fills st; returns the Newton outcome.
+sdme_status newton_core(sdme_ctx* ctx, double* u, const double* P_next_dev, double b1, const double* mhat,
+                        const sdme_newton_opts& o, sdme_step_stats& st) {
+  const int64_t nd = ctx->ndof;
+  cudaStream_t s = ctx->stream;
+  double pn2 = 0.0;
+  SDME_TRY(norm2_host(ctx, P_next_dev, &pn2));
+  const double pnorm = std::sqrt(pn2);
+  const double inner_rtol = (ctx->prec == SDME_MIXED_FP32) ? o.mixed_rtol : o.pcg_rtol;
+  double psi0 = -1.0;
+  sdme_status result = SDME_NEWTON_DIVERGED;
+  for (int k = 0; k <= o.max_newton; ++k) {
+    SDME_TRY(residual_launch(ctx, b1, u, ctx->y));
+    k_residual_combine<<<kVecBlocks, kVecThreads, 0, s>>>(ctx->mi, P_next_dev, mhat, ctx->y, ctx->psi,
+                                                        ctx->partial, ctx->dcount, ctx->dscal);
+    SDME_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 1;
+    SDME_CUDA(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SDME_TRY(sync_and_check(ctx));
+    const double nrm = std::sqrt(ctx->dscal_h[0]);
+    if (!std::isfinite(nrm)) {
+      result = SDME_NAN;
+      break;
+    }
+    if (psi0 < 0.0) psi0 = nrm;
+    if (k < 33) st.residuals[k] = nrm;
+    st.residual_final = nrm;
+    st.newton_iters = k;
+    if (nrm <= o.newton_tol * std::max(psi0, 1e-14 * pnorm)) {
+      result = SDME_OK;
+      st.converged = 1;
+      break;
+    }
+    if (k == o.max_newton) break;
+    int its = 0;
+    double rel = 0.0;
+    sdme_status ps = pcg_dispatch(ctx, b1, ctx->psi, ctx->du, inner_rtol, o.pcg_maxit, &its, &rel);
+    if (ps != SDME_OK && ps != SDME_PCG_MAXIT) {
+      result = ps;
+      break;
+    }
+    if (k < 32) st.pcg_iters[k] = its;
+    st.pcg_iters_total += its;
+    st.matvecs += its;
+    k_axpy<double><<<kVecBlocks, kVecThreads, 0, s>>>(nd, 1.0, ctx->du, u);
+    SDME_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 1;
+  }
+  st.residual0 = psi0;
+  return result;
+}
+
 extern "C" {
 
 const char* sdme_status_string(sdme_status s) {
@@ -788,54 +842,26 @@ sdme_status sdme_implicit_newmark_step(sdme_ctx* ctx, sdme_state* state, double 
   SDME_CUDA(cudaGetLastError());
   ctx->kernel_launches += 1;
   SDME_TRY(sdme_mass_apply(ctx, ctx->ahat, ctx->mhat));
-  double pn2 = 0.0;
-  SDME_TRY(norm2_host(ctx, P_next_dev, &pn2));
-  const double pnorm = std::sqrt(pn2);
-  const double inner_rtol = (ctx->prec == SDME_MIXED_FP32) ? o.mixed_rtol : o.pcg_rtol;
-  double psi0 = -1.0;
-  sdme_status result = SDME_NEWTON_DIVERGED;
-  for (int k = 0; k <= o.max_newton; ++k) {
-    SDME_TRY(residual_launch(ctx, b1, state->u, ctx->y));
-    k_residual_combine<<<kVecBlocks, kVecThreads, 0, s>>>(ctx->mi, P_next_dev, ctx->mhat, ctx->y, ctx->psi,
-                                                        ctx->partial, ctx->dcount, ctx->dscal);
-    SDME_CUDA(cudaGetLastError());
-    ctx->kernel_launches += 1;
-    SDME_CUDA(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, s));
-    SDME_TRY(sync_and_check(ctx));
-    const double nrm = std::sqrt(ctx->dscal_h[0]);
-    if (!std::isfinite(nrm)) {
-      result = SDME_NAN;
-      break;
-    }
-    if (psi0 < 0.0) psi0 = nrm;
-    if (k < 33) st.residuals[k] = nrm;
-    st.residual_final = nrm;
-    st.newton_iters = k;
-    if (nrm <= o.newton_tol * std::max(psi0, 1e-14 * pnorm)) {
-      result = SDME_OK;
-      st.converged = 1;
-      break;
-    }
-    if (k == o.max_newton) break;
-    int its = 0;
-    double rel = 0.0;
-    sdme_status ps = pcg_dispatch(ctx, b1, ctx->psi, ctx->du, inner_rtol, o.pcg_maxit, &its, &rel);
-    if (ps != SDME_OK && ps != SDME_PCG_MAXIT) {
-      result = ps;
-      break;
-    }
-    if (k < 32) st.pcg_iters[k] = its;
-    st.pcg_iters_total += its;
-    st.matvecs += its;
-    k_axpy<double><<<kVecBlocks, kVecThreads, 0, s>>>(nd, 1.0, ctx->du, state->u);
-    SDME_CUDA(cudaGetLastError());
-    ctx->kernel_launches += 1;
-  }
-  st.residual0 = psi0;
+  const sdme_status result = newton_core(ctx, state->u, P_next_dev, b1, ctx->mhat, o, st);
+  if (result == SDME_ECUDA || result == SDME_NONPOSITIVE_J) return result;
   k_newmark_final<<<kVecBlocks, kVecThreads, 0, s>>>(nd, state->u, ctx->ahat, b1, dt, o.gamma, state->v, state->a);
   SDME_CUDA(cudaGetLastError());
   ctx->kernel_launches += 1;
   SDME_CUDA(cudaStreamSynchronize(s));
+  if (stats) *stats = st;
+  return result;
+}
+
+sdme_status sdme_static_solve(sdme_ctx* ctx, double* u_dev, const double* P_dev, const sdme_newton_opts* opts,
+                              sdme_step_stats* stats) {
+  if (!ctx || !u_dev || !P_dev) return SDME_EINVAL;
+  sdme_newton_opts o{0.25, 0.5, 1e-8, 50, 1e-12, 1e-4, 20000};
+  if (opts) o = *opts;
+  if (o.max_newton < 0 || o.pcg_maxit < 1) return SDME_EINVAL;
+  sdme_step_stats st{};
+  const sdme_status result = newton_core(ctx, u_dev, P_dev, 0.0, nullptr, o, st);
+  if (result == SDME_ECUDA || result == SDME_NONPOSITIVE_J) return result;
+  SDME_CUDA(cudaStreamSynchronize(ctx->stream));
   if (stats) *stats = st;
   return result;
 }
