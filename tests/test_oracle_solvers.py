@@ -138,3 +138,26 @@ def test_newmark_linear_energy_conservation():
         u, v, a, st = solvers.newmark_step(d, u, v, a, np.zeros(d.mesh.ndof), 0.01, tol=1e-12,
                                            linear="direct")
     assert abs(energy(u, v) - E0) < 1e-6 * E0
+
+
+def test_newmark_fabricated_matches_paper_table():
+    # Sec. 5.2.2: Newmark + SDME-H on the explicit study's field, P = 2
+    with open(os.path.join(GOLDEN, "newmark_fab_l2.json")) as fh:
+        g = json.load(fh)
+    P = 2
+    row = [r for r in g["rows"] if r[0] == P][0]
+    d = Discretization(BoxMesh(2, 2, 2, P).clamp("xmin"), Basis1D(P, "sdme_h"), MU, LAM)
+    fld = manufactured.sine_field()
+    dt = g["dt"]
+    N = int(round(g["T"] / dt))
+    u = np.zeros(d.mesh.ndof)
+    v = d.l2_project(fld.velocity, 0.0)
+    v[d.mask] = 0.0
+    a = solvers.initial_acceleration(d, u, manufactured.load_vector(d, fld, 0.0))
+    for n in range(N):
+        u, v, a, st = solvers.newmark_step(d, u, v, a, manufactured.load_vector(d, fld, (n + 1) * dt), dt,
+                                           tol=1e-11, linear="direct")
+        assert st["converged"]
+    err = d.l2_error(u, fld.displacement, g["T"])
+    for have, want in zip(err, row[2:]):
+        assert want / 3.0 < have < want * 3.0, (err, row)
