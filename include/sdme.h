@@ -223,6 +223,24 @@ sdme_status sdme_pcg_solve(sdme_ctx* ctx, const double* u_dev, double b1, const 
 sdme_status sdme_traction_load(sdme_ctx* ctx, int face, const double t[3], double* f_dev);
 
 /*
+ * Static condensation of the element-interior modes (the paper's solver
+ * shape: Schur complement on the tangent matrix and residual, Sec. 4 and
+ * Sec. 5.1).  When enabled, every effective-operator solve (sdme_pcg_solve,
+ * the Newton iterations of sdme_implicit_newmark_step and sdme_static_solve)
+ * forms the dense element matrices, factors their interior blocks
+ * (Cholesky), builds the element Schur complements S_e = A_BB - A_BI A_II^-1
+ * A_IB, runs Jacobi-PCG (diagonal of S) on the skeleton DOFs and recovers
+ * the interior DOFs; iteration counts then refer to the condensed system.
+ * Interior DOFs: lattice points none of whose indices is a multiple of P.
+ * Memory: nelem (N^2 + Ni^2 + Ni Nb + Nb^2) float64 words, N = 3 (P+1)^3,
+ * Ni = 3 (P-1)^3, Nb = N - Ni (about 67 MB per element at P = 8, 1.7 MB at
+ * P = 4).  Float64 contexts only, P >= 2, at most 65535 elements, not for
+ * SDME_NODAL_LUMPED (else SDME_EUNSUPPORTED); SDME_ENOMEM if the buffers do
+ * not fit.  enable = 0 returns to the uncondensed path (buffers are kept).
+ */
+sdme_status sdme_set_condensation(sdme_ctx* ctx, int enable);
+
+/*
  * Static equilibrium R(u) = P by Newton-Raphson without inertia (the static
  * problem of Sec. 5.1): psi = P - R(u), K_T(u) du = psi by Jacobi-PCG (rtol
  * pcg_rtol in FP64, mixed_rtol in MIXED_FP32), u += du, until

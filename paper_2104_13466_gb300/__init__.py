@@ -36,7 +36,8 @@ EXPORTS = ("sdme_status_string", "sdme_build_basis1d", "sdme_create", "sdme_dest
            "sdme_set_material", "sdme_internal_force_vjp", "sdme_tape_create", "sdme_tape_destroy",
            "sdme_explicit_forward", "sdme_explicit_adjoint", "sdme_batch_create", "sdme_batch_destroy",
            "sdme_batch_layout", "sdme_batch_internal_force", "sdme_batch_tangent_apply", "sdme_batch_traction_load",
-           "sdme_batch_newmark_step", "sdme_batch_tune", "sdme_batch_launches", "sdme_static_solve")
+           "sdme_batch_newmark_step", "sdme_batch_tune", "sdme_batch_launches", "sdme_static_solve",
+           "sdme_set_condensation")
 
 
 class BasisDesc(ctypes.Structure):
@@ -134,6 +135,7 @@ def _load():
                                     ctypes.POINTER(ctypes.c_float)]
     lib.sdme_batch_launches.argtypes = [vp, i64p]
     lib.sdme_static_solve.argtypes = [vp, vp, vp, ctypes.POINTER(NewtonOpts), ctypes.POINTER(StepStats)]
+    lib.sdme_set_condensation.argtypes = [vp, i]
     lib.sdme_set_timing.argtypes = [vp, i]
     lib.sdme_get_timing.argtypes = [vp, ctypes.POINTER(Timing)]
     lib.sdme_tangent_apply_noalloc.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(Material), i, pd, pd, pd,
@@ -333,6 +335,11 @@ class Context:
                                                 ctypes.byref(opts), ctypes.byref(stats))
         _check(status, "sdme_implicit_newmark_step", allow=allow, ctx=self._h)
         return _stats_dict(stats, status)
+
+    def set_condensation(self, enable=True):
+        """Static condensation of the element-interior modes for every
+        effective-operator solve (sdme_set_condensation)."""
+        return _check(lib.sdme_set_condensation(self._h, int(bool(enable))), "sdme_set_condensation", ctx=self._h)
 
     def static_solve(self, u, P, newton_tol=1e-8, max_newton=50, pcg_rtol=1e-12, mixed_rtol=1e-4, pcg_maxit=20000,
                      allow=()):

@@ -13,6 +13,7 @@
 #include "basis1d.h"
 #include "common.cuh"
 #include "elem_launch.h"
+#include "cond_dense.cuh"
 #include "eo_tables.h"
 #include "vec_kernels.cuh"
 
@@ -69,6 +70,12 @@ struct sdme_ctx {
   double *un = nullptr, *ahat = nullptr, *mhat = nullptr, *y = nullptr, *psi = nullptr, *du = nullptr;
   // lumped (diagonal) mass of SDME_NODAL_LUMPED contexts, else null
   double* mlump = nullptr;
+  // static condensation of the element-interior modes (sdme_set_condensation)
+  bool cond = false;
+  int cN = 0, cNi = 0, cNb = 0;
+  int *cIl = nullptr, *cBl = nullptr, *cerr = nullptr;
+  int64_t *cgI = nullptr, *cgB = nullptr;
+  double *cKe = nullptr, *cL = nullptr, *cW = nullptr, *cS = nullptr, *cY = nullptr, *cg = nullptr;
   // pinned host mirrors
   PcgScalars* scal_h = nullptr;
   double* dscal_h = nullptr;
@@ -80,7 +87,7 @@ struct sdme_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t gexec[1] = {nullptr};   // one chunk of PCG iterations (untimed mode)
   double gb1[1] = {0.0};
-  bool gmass = false;
+  int gop = 0;
   int gsize = 0;
 
   // measurement
@@ -192,11 +199,24 @@ sdme_status norm2_host(sdme_ctx* ctx, const double* x, double* out) {
   return SDME_OK;
 }
 
-// Issue one chunk of PCG iterations (tangent, update, direction) on ctx->stream.
+// Operators the PCG core can iterate on.
+enum PcgOp { kOpTangent = 0, kOpMass = 1, kOpCondensed = 2 };
+
+// Issue one chunk of PCG iterations (operator, update, direction) on ctx->stream.
 template <typename T, typename TV>
-sdme_status pcg_chunk(sdme_ctx* ctx, double b1, bool mass_only, bool tim, TV* r, TV* p, TV* q, TV* dinv, TV* xv) {
+sdme_status pcg_chunk(sdme_ctx* ctx, double b1, int op, bool tim, TV* r, TV* p, TV* q, TV* dinv, TV* xv) {
   for (int j = 0; j < kPcgChunk; ++j) {
-    if (mass_only) {
+    if (op == kOpCondensed) {
+      if constexpr (sizeof(TV) == 8) {
+        if (tim) SDME_CUDA(cudaEventRecord(ctx->ev[2 * j], ctx->stream));
+        cond_apply_kernel<<<ctx->h.nelem, 256, sizeof(double) * ctx->cNb, ctx->stream>>>(
+            ctx->cNb, ctx->cgB, ctx->cS, p, q, ctx->partial, ctx->scal);
+        if (tim) SDME_CUDA(cudaEventRecord(ctx->ev[2 * j + 1], ctx->stream));
+        ctx->kernel_launches += 1;
+      } else {
+        return SDME_EUNSUPPORTED;
+      }
+    } else if (op == kOpMass) {
       SDME_CUDA(dispatch_P(ctx->h.P, [&](auto Pc) {
         return launch_mass_op<decltype(Pc)::value, T, TV>(ctx->h, b1, p, q, ctx->partial, ctx->scal, ctx->stream);
       }));
@@ -237,10 +257,10 @@ struct SideStreamScope {
 // (kernels see the device-side status and return at once after convergence);
 // the host reads the status between chunks.
 template <typename T, typename TV>
-sdme_status pcg_core(sdme_ctx* ctx, double b1, bool mass_only, const double* b, double* x, double rtol, int maxit,
+sdme_status pcg_core(sdme_ctx* ctx, double b1, int op, const double* b, double* x, double rtol, int maxit,
                      int* iters, double* rel, TV* r, TV* p, TV* q, TV* dinv, TV* xv) {
   SideStreamScope scope(ctx);
-  if (mass_only) {
+  if (op == kOpMass) {
     SDME_CUDA(cudaMemsetAsync(dinv, 0, sizeof(TV) * ctx->ndof, ctx->stream));
     SDME_CUDA(dispatch_P(ctx->h.P, [&](auto Pc) {
       return launch_mass_diag<decltype(Pc)::value, T>(ctx->h, b1, (T*)dinv, ctx->stream);
@@ -248,9 +268,9 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, bool mass_only, const double* b, 
     k_diag_finish<T><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, (T*)dinv, 1);
     SDME_CUDA(cudaGetLastError());
     ctx->kernel_launches += 2;
-  } else {
+  } else if (op == kOpTangent) {
     SDME_TRY(diag_launch<T>(ctx, b1, (T*)dinv, 1));
-  }
+  }  // kOpCondensed: the caller has put 1 / diag(S) in dinv
   k_pcg_init<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, b, 1.0, dinv, xv, r, p, q, ctx->scal,
                                                               ctx->partial, rtol, maxit);
   SDME_CUDA(cudaGetLastError());
@@ -265,19 +285,19 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, bool mass_only, const double* b, 
     // timed mode issues the chunk directly; the untimed mode replays a graph.
     const bool tim = ctx->timing;
     cudaGraphExec_t& ge = ctx->gexec[0];
-    if (ge && (ctx->gb1[0] != b1 || ctx->gmass != mass_only || ctx->gsize != (int)sizeof(T))) {
+    if (ge && (ctx->gb1[0] != b1 || ctx->gop != op || ctx->gsize != (int)sizeof(T))) {
       cudaGraphExecDestroy(ge);
       ge = nullptr;
     }
     if (tim) {
-      SDME_TRY((pcg_chunk<T, TV>(ctx, b1, mass_only, true, r, p, q, dinv, xv)));
+      SDME_TRY((pcg_chunk<T, TV>(ctx, b1, op, true, r, p, q, dinv, xv)));
     } else if (!ge) {
       // first chunk runs directly (also sets the kernels' attributes), then
       // the same chunk is captured for the following ones
-      SDME_TRY((pcg_chunk<T, TV>(ctx, b1, mass_only, false, r, p, q, dinv, xv)));
+      SDME_TRY((pcg_chunk<T, TV>(ctx, b1, op, false, r, p, q, dinv, xv)));
       cudaGraph_t g = nullptr;
       SDME_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-      sdme_status cs = pcg_chunk<T, TV>(ctx, b1, mass_only, false, r, p, q, dinv, xv);
+      sdme_status cs = pcg_chunk<T, TV>(ctx, b1, op, false, r, p, q, dinv, xv);
       cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
       if (cs != SDME_OK) return cs;
       SDME_CUDA(ce);
@@ -285,7 +305,7 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, bool mass_only, const double* b, 
       cudaGraphDestroy(g);
       SDME_CUDA(ce);
       ctx->gb1[0] = b1;
-      ctx->gmass = mass_only;
+      ctx->gop = op;
       ctx->gsize = (int)sizeof(T);
     } else {
       SDME_CUDA(cudaGraphLaunch(ge, ctx->stream));
@@ -328,10 +348,11 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, bool mass_only, const double* b, 
 
 sdme_status pcg_dispatch(sdme_ctx* ctx, double b1, const double* b, double* x, double rtol, int maxit,
                          int* iters, double* rel, bool mass_only = false) {
+  const int op = mass_only ? kOpMass : kOpTangent;
   if (ctx->prec == SDME_MIXED_FP32)
-    return pcg_core<float, float>(ctx, b1, mass_only, b, x, rtol, maxit, iters, rel, ctx->r32, ctx->p32, ctx->q32,
+    return pcg_core<float, float>(ctx, b1, op, b, x, rtol, maxit, iters, rel, ctx->r32, ctx->p32, ctx->q32,
                                   ctx->d32, ctx->x32);
-  return pcg_core<double, double>(ctx, b1, mass_only, b, x, rtol, maxit, iters, rel, ctx->r64, ctx->p64, ctx->q64,
+  return pcg_core<double, double>(ctx, b1, op, b, x, rtol, maxit, iters, rel, ctx->r64, ctx->p64, ctx->q64,
                                   ctx->d64, ctx->x64);
 }
 
@@ -348,6 +369,54 @@ sdme_status mass_solve_core(sdme_ctx* ctx, const double* b, double* x, double rt
     return SDME_OK;
   }
   return pcg_dispatch(ctx, 1.0, b, x, rtol, maxit, iters, rel, true);
+}
+
+// (b1 M + K_T(u)) x = f through the Schur complement on the skeleton DOFs
+// (linearisation state at u already stored): dense element matrices, their
+// interior factorisation and element Schur complements, Jacobi-PCG on the
+// condensed system, interior recovery.  Float64 contexts only.
+sdme_status cond_solve(sdme_ctx* ctx, double b1, const double* f, double* x, double rtol, int maxit, int* iters,
+                       double* rel) {
+  const int ne = ctx->h.nelem, N = ctx->cN, Ni = ctx->cNi, Nb = ctx->cNb;
+  cudaStream_t s = ctx->stream;
+  SDME_CUDA(dispatch_P(ctx->h.P, [&](auto Pc) {
+    return launch_cond_columns<decltype(Pc)::value>(ctx->h, b1, ctx->st64, ctx->cKe, s);
+  }));
+  SDME_CUDA(cudaMemsetAsync(ctx->cerr, 0, sizeof(int) * ne, s));
+  cond_factor_kernel<<<ne, kCondThreads, 0, s>>>(N, Ni, ctx->cIl, ctx->cKe, ctx->cL, ctx->cerr);
+  cond_trsm_kernel<<<ne, kCondThreads, 0, s>>>(N, Ni, Nb, ctx->cIl, ctx->cBl, ctx->cKe, ctx->cL, ctx->cW);
+  const unsigned tiles = (unsigned)((Nb + 31) / 32);
+  cond_syrk_kernel<<<dim3(tiles, tiles, ne), dim3(32, 32), 0, s>>>(N, Ni, Nb, ctx->cBl, ctx->cKe, ctx->cW, ctx->cS);
+  SDME_CUDA(cudaGetLastError());
+  // 1 / diag(S) (interior entries 1), condensed right-hand side
+  SDME_CUDA(cudaMemsetAsync(ctx->d64, 0, sizeof(double) * ctx->ndof, s));
+  cond_diag_kernel<<<ne, 256, 0, s>>>(Nb, ctx->cgB, ctx->cS, ctx->d64);
+  cond_rhs_init<<<kVecBlocks, 256, 0, s>>>(ctx->mi, ctx->h.P, f, ctx->cg, ctx->d64);
+  k_diag_finish<double><<<kVecBlocks, kVecThreads, 0, s>>>(ctx->mi, ctx->d64, 1);
+  cond_rhs_kernel<<<ne, 256, sizeof(double) * Ni, s>>>(Ni, Nb, ctx->cgI, ctx->cgB, ctx->cL, ctx->cW, f, ctx->cg,
+                                                       ctx->cY);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 9;
+  std::vector<int> errs(ne);
+  SDME_CUDA(cudaMemcpyAsync(errs.data(), ctx->cerr, sizeof(int) * ne, cudaMemcpyDeviceToHost, s));
+  SDME_CUDA(cudaStreamSynchronize(s));
+  for (int v : errs)
+    if (v) return SDME_NAN;  // interior block not positive definite
+  const sdme_status ps = pcg_core<double, double>(ctx, b1, kOpCondensed, ctx->cg, x, rtol, maxit, iters, rel,
+                                                  ctx->r64, ctx->p64, ctx->q64, ctx->d64, ctx->x64);
+  if (ps != SDME_OK && ps != SDME_PCG_MAXIT) return ps;
+  cond_recover_kernel<<<ne, 256, sizeof(double) * (Ni + Nb), s>>>(Ni, Nb, ctx->cgI, ctx->cgB, ctx->cL, ctx->cW,
+                                                                  ctx->cY, x);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 1;
+  return ps;
+}
+
+// The effective-operator solve of the Newton iteration and of sdme_pcg_solve.
+sdme_status linear_solve(sdme_ctx* ctx, double b1, const double* f, double* x, double rtol, int maxit, int* iters,
+                         double* rel) {
+  if (ctx->cond) return cond_solve(ctx, b1, f, x, rtol, maxit, iters, rel);
+  return pcg_dispatch(ctx, b1, f, x, rtol, maxit, iters, rel);
 }
 
 // Lumped mass of SDME_NODAL_LUMPED: rho detJ w_p w_q w_r (GLL weights) per
@@ -392,7 +461,9 @@ sdme_status dot_host(sdme_ctx* ctx, const double* x, const double* y, double* ou
 void free_all(sdme_ctx* ctx) {
   void* dev[] = {ctx->st64, ctx->st32, ctx->err, ctx->scal, ctx->partial, ctx->dscal, ctx->dcount,
                  ctx->r64, ctx->p64, ctx->q64, ctx->d64, ctx->x64, ctx->r32, ctx->p32, ctx->q32, ctx->d32,
-                 ctx->x32, ctx->un, ctx->ahat, ctx->mhat, ctx->y, ctx->psi, ctx->du, ctx->mlump};
+                 ctx->x32, ctx->un, ctx->ahat, ctx->mhat, ctx->y, ctx->psi, ctx->du, ctx->mlump,
+                 ctx->cIl, ctx->cBl, ctx->cerr, ctx->cgI, ctx->cgB, ctx->cKe, ctx->cL, ctx->cW, ctx->cS,
+                 ctx->cY, ctx->cg};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (ctx->scal_h) cudaFreeHost(ctx->scal_h);
@@ -508,7 +579,7 @@ sdme_status newton_core(sdme_ctx* ctx, double* u, const double* P_next_dev, doub
     if (k == o.max_newton) break;
     int its = 0;
     double rel = 0.0;
-    sdme_status ps = pcg_dispatch(ctx, b1, ctx->psi, ctx->du, inner_rtol, o.pcg_maxit, &its, &rel);
+    sdme_status ps = linear_solve(ctx, b1, ctx->psi, ctx->du, inner_rtol, o.pcg_maxit, &its, &rel);
     if (ps != SDME_OK && ps != SDME_PCG_MAXIT) {
       result = ps;
       break;
@@ -732,6 +803,78 @@ sdme_status sdme_set_material(sdme_ctx* ctx, const sdme_material* mat) {
   return SDME_OK;
 }
 
+sdme_status sdme_set_condensation(sdme_ctx* ctx, int enable) {
+  if (!ctx) return SDME_EINVAL;
+  if (!enable) {
+    ctx->cond = false;
+    return SDME_OK;
+  }
+  if (ctx->cond) return SDME_OK;
+  const HostElemData& h = ctx->h;
+  const int P = h.P, n = P + 1, n3 = n * n * n;
+  if (ctx->prec != SDME_FP64 || ctx->mlump || P < 2 || h.nelem > 65535) return SDME_EUNSUPPORTED;
+  const int N = 3 * n3, Ni = 3 * (n - 2) * (n - 2) * (n - 2), Nb = N - Ni;
+  std::vector<int> Il, Bl;
+  for (int idx = 0; idx < N; ++idx) {
+    const int m = idx % n3, p = m % n, q = (m / n) % n, r = m / (n * n);
+    const bool inner = p > 0 && p < n - 1 && q > 0 && q < n - 1 && r > 0 && r < n - 1;
+    (inner ? Il : Bl).push_back(idx);
+  }
+  const int ne = h.nelem;
+  std::vector<int64_t> gI((size_t)ne * Ni), gB((size_t)ne * Nb);
+  for (int e = 0; e < ne; ++e) {
+    const int ex = e % h.ne[0], ey = (e / h.ne[0]) % h.ne[1], ez = e / (h.ne[0] * h.ne[1]);
+    auto global = [&](int idx, bool* cons) {
+      const int c = idx / n3, m = idx % n3, p = m % n, q = (m / n) % n, r = m / (n * n);
+      const int ix = ex * P + p, iy = ey * P + q, iz = ez * P + r;
+      const unsigned bit = 1u << c;
+      *cons = (ix == 0 && (h.clamp[0] & bit)) || (ix == h.N[0] - 1 && (h.clamp[1] & bit)) ||
+              (iy == 0 && (h.clamp[2] & bit)) || (iy == h.N[1] - 1 && (h.clamp[3] & bit)) ||
+              (iz == 0 && (h.clamp[4] & bit)) || (iz == h.N[2] - 1 && (h.clamp[5] & bit));
+      return c * h.Nn + ((int64_t)iz * h.N[1] + iy) * h.N[0] + ix;
+    };
+    bool cons;
+    for (int i = 0; i < Ni; ++i) gI[(size_t)e * Ni + i] = global(Il[i], &cons);
+    for (int b = 0; b < Nb; ++b) {
+      const int64_t g = global(Bl[b], &cons);
+      gB[(size_t)e * Nb + b] = cons ? -1 : g;
+    }
+  }
+  bool ok = dalloc(&ctx->cIl, Ni) == cudaSuccess && dalloc(&ctx->cBl, Nb) == cudaSuccess &&
+            dalloc(&ctx->cerr, ne) == cudaSuccess && dalloc(&ctx->cgI, (size_t)ne * Ni) == cudaSuccess &&
+            dalloc(&ctx->cgB, (size_t)ne * Nb) == cudaSuccess &&
+            dalloc(&ctx->cKe, (size_t)ne * N * N) == cudaSuccess &&
+            dalloc(&ctx->cL, (size_t)ne * Ni * Ni) == cudaSuccess &&
+            dalloc(&ctx->cW, (size_t)ne * Ni * Nb) == cudaSuccess &&
+            dalloc(&ctx->cS, (size_t)ne * Nb * Nb) == cudaSuccess &&
+            dalloc(&ctx->cY, (size_t)ne * Ni) == cudaSuccess && dalloc(&ctx->cg, ctx->ndof) == cudaSuccess;
+  if (ok) {
+    cudaStream_t s = ctx->stream;
+    ok = cudaMemcpyAsync(ctx->cIl, Il.data(), sizeof(int) * Ni, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+         cudaMemcpyAsync(ctx->cBl, Bl.data(), sizeof(int) * Nb, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+         cudaMemcpyAsync(ctx->cgI, gI.data(), sizeof(int64_t) * gI.size(), cudaMemcpyHostToDevice, s) ==
+             cudaSuccess &&
+         cudaMemcpyAsync(ctx->cgB, gB.data(), sizeof(int64_t) * gB.size(), cudaMemcpyHostToDevice, s) ==
+             cudaSuccess &&
+         cudaStreamSynchronize(s) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    for (void* p : {(void*)ctx->cIl, (void*)ctx->cBl, (void*)ctx->cerr, (void*)ctx->cgI, (void*)ctx->cgB,
+                    (void*)ctx->cKe, (void*)ctx->cL, (void*)ctx->cW, (void*)ctx->cS, (void*)ctx->cY, (void*)ctx->cg})
+      if (p) cudaFree(p);
+    ctx->cIl = ctx->cBl = ctx->cerr = nullptr;
+    ctx->cgI = ctx->cgB = nullptr;
+    ctx->cKe = ctx->cL = ctx->cW = ctx->cS = ctx->cY = ctx->cg = nullptr;
+    return SDME_ENOMEM;
+  }
+  ctx->cN = N;
+  ctx->cNi = Ni;
+  ctx->cNb = Nb;
+  ctx->cond = true;
+  return SDME_OK;
+}
+
 sdme_status sdme_internal_force_vjp(sdme_ctx* ctx, const double* u_dev, const double* w_dev, double* gu_dev,
                                     double* gmu, double* glambda) {
   if (!ctx || !u_dev || !w_dev || !gu_dev) return SDME_EINVAL;
@@ -791,7 +934,7 @@ sdme_status sdme_pcg_solve(sdme_ctx* ctx, const double* u_dev, double b1, const 
   if (ctx->mlump && b1 != 0.0) return SDME_EUNSUPPORTED;
   SDME_TRY(residual_launch(ctx, 0.0, u_dev, ctx->y));
   SDME_TRY(sync_and_check(ctx));
-  return pcg_dispatch(ctx, b1, b_dev, x_dev, rtol, maxit, iters, final_rel);
+  return linear_solve(ctx, b1, b_dev, x_dev, rtol, maxit, iters, final_rel);
 }
 
 sdme_status sdme_traction_load(sdme_ctx* ctx, int face, const double t[3], double* f_dev) {

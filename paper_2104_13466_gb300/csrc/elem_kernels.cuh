@@ -655,30 +655,15 @@ constexpr int tangent_min_blocks() {
 // dot_partial / scal (both optional) couple the launch to one PCG solve:
 // dot_partial[e] receives x_e . (K_e x_e), and the last of the nparts
 // elements to finish writes p.q and the step length into *scal.
-template <int P, typename T, typename TV, bool STIFF>
-__device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pairs, const MeshParams<T>& m, int e,
-                                             const TV* __restrict__ x, TV* __restrict__ y,
-                                             const T* __restrict__ st, double* __restrict__ dot_partial,
-                                             unsigned nparts, PcgScalars* __restrict__ scal, T* sm) {
+// The tangent action on the element coefficients held in X (the gather's
+// shared layout): forward stages, pointwise linearised stress (and the fused
+// mass term), transposed stages; the result replaces X.
+template <int P, typename T, bool STIFF>
+__device__ __forceinline__ void tangent_core(const ElemTables<T, P>& tb, int pairs, const MeshParams<T>& m, int e,
+                                             const T* __restrict__ st, T* sm) {
   using G = Geo<P>;
-  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
-  constexpr int NT = G::NT;  // == blockDim.x: compile-time strides let the loops batch their loads
-  if (scal && scal->status != 0) return;
-  if constexpr (STIFF) {
-    // start pulling the element's linearisation state into L2 now; the
-    // pointwise stage reads it after the gather and the forward stages
-    if (threadIdx.x == 0) prefetch_l2(st + (int64_t)e * kStateFields * Q3, sizeof(T) * kStateFields * Q3);
-  }
-  T* X = sm + 3 * FQ;
-  const ElemView<MeshParams<T>> view(m, P, e);
-#pragma unroll
-  for (int idx = threadIdx.x; idx < 3 * n3; idx += NT) {
-    bool cons;
-    int so;
-    const int64_t g = entry_index<P>(m, view, idx, &cons, &so);
-    X[so] = cons ? T(0) : (T)x[g];
-  }
-  __syncthreads();
+  constexpr int Q = P + 2, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
+  constexpr int NT = G::NT;
   forward_stages<T, P, STIFF>(tb, pairs, sm);
   const T sc[3] = {m.s[0], m.s[1], m.s[2]};
   const T* ste = st + (int64_t)e * kStateFields * Q3;
@@ -730,6 +715,33 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
   }
   __syncthreads();
   transpose_stages<T, P, STIFF>(tb, pairs, sm);
+}
+
+template <int P, typename T, typename TV, bool STIFF>
+__device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pairs, const MeshParams<T>& m, int e,
+                                             const TV* __restrict__ x, TV* __restrict__ y,
+                                             const T* __restrict__ st, double* __restrict__ dot_partial,
+                                             unsigned nparts, PcgScalars* __restrict__ scal, T* sm) {
+  using G = Geo<P>;
+  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, FQ = G::FQ;
+  constexpr int NT = G::NT;  // == blockDim.x: compile-time strides let the loops batch their loads
+  if (scal && scal->status != 0) return;
+  if constexpr (STIFF) {
+    // start pulling the element's linearisation state into L2 now; the
+    // pointwise stage reads it after the gather and the forward stages
+    if (threadIdx.x == 0) prefetch_l2(st + (int64_t)e * kStateFields * Q3, sizeof(T) * kStateFields * Q3);
+  }
+  T* X = sm + 3 * FQ;
+  const ElemView<MeshParams<T>> view(m, P, e);
+#pragma unroll
+  for (int idx = threadIdx.x; idx < 3 * n3; idx += NT) {
+    bool cons;
+    int so;
+    const int64_t g = entry_index<P>(m, view, idx, &cons, &so);
+    X[so] = cons ? T(0) : (T)x[g];
+  }
+  __syncthreads();
+  tangent_core<P, T, STIFF>(tb, pairs, m, e, st, sm);
   T dotT = T(0);
 #pragma unroll
   for (int idx = threadIdx.x; idx < 3 * n3; idx += NT) {

@@ -62,6 +62,9 @@ cudaError_t launch_batch_mass(const HostElemData& tabs, const HostBatchLaunch& L
                               double* y, cudaStream_t s);
 
 template <int P>
+cudaError_t launch_cond_columns(const HostElemData& h, double b1, const double* st, double* Ke, cudaStream_t s);
+
+template <int P>
 cudaError_t launch_residual(const HostElemData& h, double b1, const double* u, double* y, double* st64,
                             float* st32, int* err, cudaStream_t s);
 template <int P, typename T, typename TV>

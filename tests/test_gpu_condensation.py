@@ -1,0 +1,137 @@
+"""GPU parity of the statically condensed solver (Schur complement on the
+element-interior modes) against the oracle's condensed solve, and the
+paper's CGD iteration counts (Sec. 5.1, Table NH_average_IT_CGD) reproduced
+on the GPU.  Float64; solution tolerance 1e-9 relative (CG to 1e-13)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import condensation, manufactured, solvers  # noqa: E402
+from oracle.assembly import Discretization  # noqa: E402
+from oracle.basis1d import Basis1D  # noqa: E402
+from oracle.hexmesh import BoxMesh  # noqa: E402
+from oracle.material import lame  # noqa: E402
+
+MU, LAM = lame(1000.0, 0.3)
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _pair(P, kind, elems=(2, 2, 2), clamp=None, prec=0):
+    import paper_2104_13466_gb300 as s
+    clamp = {"xmin": (0, 1, 2)} if clamp is None else clamp
+    ctx = s.Context(elems, (1.0, 1.0, 1.0), clamp, MU, LAM, 1.0, P, kind, precision=prec)
+    mesh = BoxMesh(*elems, P)
+    for f, c in clamp.items():
+        mesh.clamp(f, c)
+    return ctx, Discretization(mesh, Basis1D(P, kind), MU, LAM, 1.0)
+
+
+@pytest.mark.parametrize("P,kind,b1", [(2, "modal", 0.0), (3, "sdme_h", 0.0), (3, "nodal", 80.0),
+                                       (4, "sdme_m", 25.0), (5, "sdme_k", 0.0)])
+def test_condensed_pcg_matches_oracle(P, kind, b1):
+    ctx, d = _pair(P, kind, elems=(2, 2, 1))
+    rng = np.random.default_rng(P)
+    u = 0.005 * rng.standard_normal(d.mesh.ndof)
+    u[d.mask] = 0.0
+    f = rng.standard_normal(d.mesh.ndof)
+    ctx.set_condensation(True)
+    x = torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda")
+    its, rel = ctx.pcg_solve(_dev(u), b1, _dev(f), x, rtol=1e-13)
+    xo, its_o = condensation.condensed_solve(d, u, f, b1=b1, rtol=1e-13)
+    xd = solvers.dense_solve(d.tangent_matrix(u, b1), np.where(d.mask, 0.0, f))
+    xg = _host(x)
+    assert np.abs(xg - xd).max() < 1e-9 * np.abs(xd).max()
+    assert np.abs(xg - xo).max() < 1e-9 * np.abs(xo).max()
+    # same algorithm on the same condensed system: iteration counts agree
+    assert abs(its - its_o) <= max(2, its_o // 50), (its, its_o)
+
+
+@pytest.mark.parametrize("P", [2, 4])
+def test_condensed_static_cgd_iterations_on_gpu(P):
+    with open(os.path.join(GOLDEN, "static_cgd_iterations.json")) as fh:
+        g = json.load(fh)
+    row = {r[0]: r[1:] for r in g["rows"]}[P]
+    got = []
+    for kind in ("modal", "sdme_m", "sdme_h"):
+        ctx, d = _pair(P, kind)
+        ctx.set_condensation(True)
+        fld = manufactured.static_field()
+        f = manufactured.load_vector(d, fld, 0.0)
+        u = torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda")
+        st = ctx.static_solve(u, _dev(f), newton_tol=1e-8, pcg_rtol=1e-12)
+        assert st["converged"] and st["newton_iters"] == 5
+        got.append(np.mean(st["pcg_iters"]))
+        uo, so = solvers.static_newton(d, f, linear="direct")
+        assert np.abs(_host(u) - uo).max() < 1e-9 * np.abs(uo).max()
+    for have, want in zip(got, row):
+        assert abs(have - want) < 0.15 * want, (got, row)
+    assert got[0] > 1.5 * got[1] and got[1] >= got[2]
+
+
+def test_condensed_newmark_matches_uncondensed():
+    ctx, d = _pair(3, "sdme_m")
+    ref, _ = _pair(3, "sdme_m")
+    ctx.set_condensation(True)
+    fld = manufactured.sine_field()
+    dt = 2e-3
+    states = []
+    for c in (ctx, ref):
+        u, v, a = (torch.zeros(c.ndof, dtype=torch.float64, device="cuda") for _ in range(3))
+        for k in range(3):
+            st = c.implicit_newmark_step(u, v, a, dt, _dev(manufactured.load_vector(d, fld, (k + 1) * dt)),
+                                         newton_tol=1e-11, pcg_rtol=1e-13)
+            assert st["converged"]
+        states.append(_host(u))
+    assert np.abs(states[0] - states[1]).max() < 1e-9 * np.abs(states[1]).max()
+
+
+def test_condensation_refused_where_unsupported():
+    import paper_2104_13466_gb300 as s
+    ctx, _ = _pair(2, "sdme_h", prec=s.MIXED_FP32)
+    with pytest.raises(s.SdmeError) as ei:
+        ctx.set_condensation(True)
+    assert ei.value.status == s.EUNSUPPORTED
+    ctx1, _ = _pair(1, "modal")
+    with pytest.raises(s.SdmeError):
+        ctx1.set_condensation(True)
+
+
+def test_condensed_newmark_cgd_iterations_on_gpu():
+    # Sec. 5.2.2, Table TransientNmk_NH_NIT_Hexa (P = 2) on the GPU
+    with open(os.path.join(GOLDEN, "newmark_cgd_iterations.json")) as fh:
+        g = json.load(fh)
+    row = {r[0]: r[1:] for r in g["rows"]}[2]
+    dt, N = g["dt"], int(round(g["T"] / g["dt"]))
+    got = []
+    for kind in ("modal", "sdme_m", "sdme_h"):
+        ctx, d = _pair(2, kind)
+        ctx.set_condensation(True)
+        fld = manufactured.sine_field()
+        v0 = d.l2_project(fld.velocity, 0.0)
+        v0[d.mask] = 0.0
+        a0 = solvers.initial_acceleration(d, np.zeros(d.mesh.ndof), manufactured.load_vector(d, fld, 0.0))
+        u = torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda")
+        v, a = _dev(v0), _dev(a0)
+        its = []
+        for k in range(N):
+            st = ctx.implicit_newmark_step(u, v, a, dt, _dev(manufactured.load_vector(d, fld, (k + 1) * dt)),
+                                           newton_tol=1e-12, pcg_rtol=1e-12)
+            assert st["converged"]
+            its += st["pcg_iters"]
+        got.append(np.mean(its))
+    for have, want in zip(got, row):
+        assert abs(have - want) < 0.15 * want, (got, row)

@@ -55,3 +55,42 @@ def test_condensed_cg_iterations_match_paper_static_table(P):
         assert abs(have - want) < 0.15 * want, (got, row)
     # the ordering the paper reports: ST >> SDME-M >= SDME-H
     assert got[0] > 1.5 * got[1] and got[1] >= got[2]
+
+
+def _newmark_condensed_iterations(P, kind, dt, T):
+    d = Discretization(BoxMesh(2, 2, 2, P).clamp("xmin"), Basis1D(P, kind), MU, LAM)
+    fld = manufactured.sine_field()
+    u = np.zeros(d.mesh.ndof)
+    v = d.l2_project(fld.velocity, 0.0)
+    v[d.mask] = 0.0
+    a = solvers.initial_acceleration(d, u, manufactured.load_vector(d, fld, 0.0))
+    b1, b2, b3 = 4.0 / dt ** 2, 4.0 / dt, 1.0
+    its = []
+    for n in range(int(round(T / dt))):
+        Pn = manufactured.load_vector(d, fld, (n + 1) * dt)
+        const = b2 * v + b3 * a
+        uk, psi0 = u.copy(), None
+        for k in range(30):
+            psi = Pn - d.mass_apply(b1 * (uk - u) - const) - d.internal_force(uk)
+            psi[d.mask] = 0.0
+            nrm = np.linalg.norm(psi)
+            psi0 = nrm if psi0 is None else psi0
+            if nrm <= 1e-12 * max(psi0, 1e-14 * np.linalg.norm(Pn)):
+                break
+            du, it = condensation.condensed_solve(d, uk, psi, b1, 1e-12)
+            its.append(it)
+            uk = uk + du
+        a_new = b1 * (uk - u) - const
+        v = v + 0.5 * dt * (a + a_new)
+        a, u = a_new, uk
+    return np.mean(its)
+
+
+def test_condensed_newmark_iterations_match_paper_table():
+    with open(os.path.join(GOLDEN, "newmark_cgd_iterations.json")) as fh:
+        g = json.load(fh)
+    row = {r[0]: r[1:] for r in g["rows"]}[2]
+    got = [_newmark_condensed_iterations(2, kind, g["dt"], g["T"]) for kind in ("modal", "sdme_m", "sdme_h")]
+    for have, want in zip(got, row):
+        assert abs(have - want) < 0.15 * want, (got, row)
+    assert got[0] > 4 * got[1]
