@@ -237,7 +237,7 @@ def run_gpu(args, w):
     a = torch.zeros_like(u)
     Pn = torch.zeros_like(u)
     opts = dict(newton_tol=w["newton_tol"], pcg_rtol=w["pcg_rtol"], mixed_rtol=args.mixed_rtol,
-                pcg_maxit=args.pcg_maxit, max_newton=args.max_newton)
+                pcg_maxit=args.pcg_maxit, max_newton=args.max_newton, forcing=args.forcing)
     nsteps = w["steps"]
     dt = w["dt"]
     step_i = [0]
@@ -389,7 +389,7 @@ def run_compare(args, w):
             smag = load_magnitude(w["load_key"])
             u, v, a, Pn = (torch.zeros_like(unit) for _ in range(4))
             opts = dict(newton_tol=w["newton_tol"], pcg_rtol=w["pcg_rtol"], mixed_rtol=args.mixed_rtol,
-                        pcg_maxit=args.pcg_maxit, max_newton=args.max_newton)
+                        pcg_maxit=args.pcg_maxit, max_newton=args.max_newton, forcing=args.forcing)
             res = []
             for k in range(1, args.warmup + args.steps + 1):
                 torch.mul(unit, smag * min(k, w["steps"]) / w["steps"], out=Pn)
@@ -702,6 +702,8 @@ def main():
     ap.add_argument("--precisions", default="mixed,fp64")
     ap.add_argument("--kernel-iters", type=int, default=20)
     ap.add_argument("--adjoint", action="store_true")
+    ap.add_argument("--forcing", type=int, default=1, choices=[0, 1],
+                    help="1: Eisenstat-Walker forcing terms for the inner PCG tolerance (0: fixed tolerance)")
     ap.add_argument("--batch", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true")

@@ -101,6 +101,12 @@ typedef struct {
   double pcg_rtol;       /* FP64: ||r|| <= rtol ||b|| */
   double mixed_rtol;     /* MIXED_FP32: inner PCG tolerance (inexact Newton) */
   int pcg_maxit;
+  int forcing;           /* 0: the inner tolerance above at every Newton iteration;
+                            1: Eisenstat-Walker forcing terms (their "choice 2":
+                            eta_k = 0.9 (|psi_k| / |psi_{k-1}|)^2 with the 0.9 eta^2
+                            safeguard, eta_0 = eta_max = 0.01, no tighter than
+                            0.5 tol |psi_0| / |psi_k|), never below the tolerance above.
+                            The Newton test itself is unchanged. */
 } sdme_newton_opts;
 
 typedef struct {
@@ -465,7 +471,8 @@ sdme_status sdme_batch_traction_load(sdme_batch* b, int face, const double* t_ho
 
 /*
  * One implicit Newmark step of every problem (as sdme_implicit_newmark_step,
- * same options for all).  Each problem runs its own Newton iteration and
+ * same options for all; the inner tolerance is the fixed one, forcing is
+ * ignored).  Each problem runs its own Newton iteration and
  * stops at its own tolerance; a problem that meets det F <= 0 or a PCG
  * breakdown stops there while the others continue.  stats (nprob entries,
  * may be NULL) receive each problem's record (converged = 0 for a problem

@@ -60,7 +60,7 @@ class Problem(ctypes.Structure):
 class NewtonOpts(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("gamma", ctypes.c_double), ("newton_tol", ctypes.c_double),
                 ("max_newton", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("mixed_rtol", ctypes.c_double),
-                ("pcg_maxit", ctypes.c_int)]
+                ("pcg_maxit", ctypes.c_int), ("forcing", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
@@ -325,11 +325,11 @@ class Context:
         return _check(lib.sdme_traction_load(self._h, face, tt, _ptr(f)), "sdme_traction_load", ctx=self._h)
 
     def implicit_newmark_step(self, u, v, a, dt, P_next, beta=0.25, gamma=0.5, newton_tol=1e-8, max_newton=30,
-                              pcg_rtol=1e-10, mixed_rtol=1e-4, pcg_maxit=20000, allow=()):
+                              pcg_rtol=1e-10, mixed_rtol=1e-4, pcg_maxit=20000, forcing=0, allow=()):
         st = State(u.data_ptr(), v.data_ptr(), a.data_ptr())
         for t in (u, v, a):
             _ptr(t)
-        opts = NewtonOpts(beta, gamma, newton_tol, max_newton, pcg_rtol, mixed_rtol, pcg_maxit)
+        opts = NewtonOpts(beta, gamma, newton_tol, max_newton, pcg_rtol, mixed_rtol, pcg_maxit, int(forcing))
         stats = StepStats()
         status = lib.sdme_implicit_newmark_step(self._h, ctypes.byref(st), float(dt), _ptr(P_next),
                                                 ctypes.byref(opts), ctypes.byref(stats))
@@ -342,9 +342,9 @@ class Context:
         return _check(lib.sdme_set_condensation(self._h, int(bool(enable))), "sdme_set_condensation", ctx=self._h)
 
     def static_solve(self, u, P, newton_tol=1e-8, max_newton=50, pcg_rtol=1e-12, mixed_rtol=1e-4, pcg_maxit=20000,
-                     allow=()):
+                     forcing=0, allow=()):
         """R(u) = P by Newton-Raphson (u: initial guess in, solution out)."""
-        opts = NewtonOpts(0.25, 0.5, newton_tol, max_newton, pcg_rtol, mixed_rtol, pcg_maxit)
+        opts = NewtonOpts(0.25, 0.5, newton_tol, max_newton, pcg_rtol, mixed_rtol, pcg_maxit, int(forcing))
         stats = StepStats()
         status = lib.sdme_static_solve(self._h, _ptr(u), _ptr(P), ctypes.byref(opts), ctypes.byref(stats))
         _check(status, "sdme_static_solve", allow=allow, ctx=self._h)
@@ -631,11 +631,11 @@ class Batch:
                                                    _ptr(f)), "sdme_batch_traction_load")
 
     def newmark_step(self, u, v, a, dt, P_next, beta=0.25, gamma=0.5, newton_tol=1e-8, max_newton=30,
-                     pcg_rtol=1e-10, mixed_rtol=1e-4, pcg_maxit=20000, allow=()):
+                     pcg_rtol=1e-10, mixed_rtol=1e-4, pcg_maxit=20000, forcing=0, allow=()):
         st = State(u.data_ptr(), v.data_ptr(), a.data_ptr())
         for t in (u, v, a):
             _ptr(t)
-        opts = NewtonOpts(beta, gamma, newton_tol, max_newton, pcg_rtol, mixed_rtol, pcg_maxit)
+        opts = NewtonOpts(beta, gamma, newton_tol, max_newton, pcg_rtol, mixed_rtol, pcg_maxit, int(forcing))
         stats = (StepStats * self.nprob)()
         status = lib.sdme_batch_newmark_step(self._h, ctypes.byref(st), float(dt), _ptr(P_next), ctypes.byref(opts),
                                              stats)

@@ -551,8 +551,8 @@ sdme_status newton_core(sdme_ctx* ctx, double* u, const double* P_next_dev, doub
   double pn2 = 0.0;
   SDME_TRY(norm2_host(ctx, P_next_dev, &pn2));
   const double pnorm = std::sqrt(pn2);
-  const double inner_rtol = (ctx->prec == SDME_MIXED_FP32) ? o.mixed_rtol : o.pcg_rtol;
-  double psi0 = -1.0;
+  const double base_rtol = (ctx->prec == SDME_MIXED_FP32) ? o.mixed_rtol : o.pcg_rtol;
+  double psi0 = -1.0, nrm_prev = -1.0, eta_prev = 0.01;
   sdme_status result = SDME_NEWTON_DIVERGED;
   for (int k = 0; k <= o.max_newton; ++k) {
     SDME_TRY(residual_launch(ctx, b1, u, ctx->y));
@@ -577,6 +577,23 @@ sdme_status newton_core(sdme_ctx* ctx, double* u, const double* P_next_dev, doub
       break;
     }
     if (k == o.max_newton) break;
+    double inner_rtol = base_rtol;
+    if (o.forcing == 1) {
+      // Eisenstat-Walker forcing term (choice 2, gamma = 0.9, alpha = 2),
+      // eta_0 = eta_max = 0.01
+      double eta = 0.01;
+      if (nrm_prev > 0.0) {
+        const double ratio = nrm / nrm_prev;
+        eta = 0.9 * ratio * ratio;
+        const double safeguard = 0.9 * eta_prev * eta_prev;
+        if (safeguard > 0.1) eta = std::max(eta, safeguard);
+      }
+      eta = std::min(eta, 0.01);
+      eta = std::max(eta, 0.5 * o.newton_tol * std::max(psi0, 1e-14 * pnorm) / nrm);
+      eta_prev = eta;
+      inner_rtol = std::max(eta, base_rtol);
+    }
+    nrm_prev = nrm;
     int its = 0;
     double rel = 0.0;
     sdme_status ps = linear_solve(ctx, b1, ctx->psi, ctx->du, inner_rtol, o.pcg_maxit, &its, &rel);

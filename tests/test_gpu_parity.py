@@ -285,3 +285,26 @@ def test_full_size_beam_sampled_tangent(prec):
     want = np.where(disc.mask[dofs], x[dofs], want)
     tol = TOL64 if prec == 0 else TOL32
     assert _relerr(yg[dofs], want) < tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_forcing_terms_reach_the_same_state(prec):
+    # Eisenstat-Walker forcing changes only the inner PCG tolerances; the
+    # Newton test (1e-10 here) decides the state
+    s = _sdme()
+    w = workload("cube_p4")
+    out = []
+    for forcing in (0, 1):
+        ctx, disc = _pair(elems=(2, 2, 2), lengths=(1.0, 1.0, 1.0), clamp={"zmin": (0, 1, 2)}, P=3, kind="sdme_h",
+                          prec=prec, E=w["E"], nu=w["nu"], rho=w["rho"])
+        f = torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda")
+        ctx.traction_load("zmax", (0.0, 0.0, -load_magnitude(w["load_key"])), f)
+        u, v, a = (torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda") for _ in range(3))
+        its = 0
+        for n in range(1, 4):
+            st = ctx.implicit_newmark_step(u, v, a, w["dt"], f * (n / 3.0), newton_tol=1e-10, forcing=forcing)
+            assert st["converged"]
+            its += st["pcg_iters_total"]
+        out.append((_host(u), its))
+    assert _relerr(out[1][0], out[0][0]) < 1e-8
+    assert out[1][1] < out[0][1]
