@@ -27,6 +27,9 @@ numpy at float64 from Dias, Suzuki, Valente, Bittencourt (arXiv:2104.13466):
 * ``manufactured`` fabricated-solution body forces and tractions (Sec. 5).
 * ``adjoint``      vector-Jacobian product of the internal force and the
                    discrete adjoint of the explicit scheme (Sec. 4.1).
+* ``condensation`` Schur complement on the element-interior modes (Sec. 4,
+                   Sec. 5.1).
+* ``quad``         plane-strain quadrilaterals (eq. ProdTensorialQuadrado).
 
 Every function whose result is not pinned to something outside itself says
 "parity unpinned" in its docstring; the tests in ``tests/test_oracle_*.py``
