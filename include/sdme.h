@@ -83,9 +83,19 @@ typedef struct {
   double jacobi_beta;
 } sdme_basis_desc;
 
+/*
+ * Box meshes of equal hexahedra; nelem[2] = 0 selects a plane-strain
+ * rectangle of equal quadrilaterals in the x-y plane instead (tensor products
+ * of eq. ProdTensorialQuadrado; F_33 = 1): two components per lattice point,
+ * vectors [2][Ny][Nx], clamp[4] = clamp[5] = 0, edges SDME_XMIN..SDME_YMAX.
+ * Two-dimensional contexts support the internal force, tangent action,
+ * diagonal, mass, PCG, static/Newmark/explicit steps, energy, critical step
+ * and edge tractions; the adjoint, body loads, condensation, lumped mass and
+ * batches are SDME_EUNSUPPORTED there.
+ */
 typedef struct {
-  int nelem[3];          /* hexahedra per direction */
-  double length[3];      /* box edge lengths */
+  int nelem[3];          /* elements per direction (nelem[2] = 0: 2D) */
+  double length[3];      /* box edge lengths (length[2] unused in 2D) */
   unsigned clamp[6];     /* per face (SDME_XMIN..SDME_ZMAX): bit c set = component c constrained */
 } sdme_mesh_desc;
 

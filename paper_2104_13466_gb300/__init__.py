@@ -195,11 +195,12 @@ def build_basis1d(P, kind, Q=None, k=0.5, lam=100.0, start_nodal=False):
 
 
 def mesh_desc(elems, lengths, clamp):
-    """clamp: dict face-name -> iterable of components."""
+    """clamp: dict face-name -> iterable of components.  Two-entry elems and
+    lengths describe a plane-strain rectangle of quadrilaterals (nelem[2] = 0)."""
     m = MeshDesc()
     for d in range(3):
-        m.nelem[d] = int(elems[d])
-        m.length[d] = float(lengths[d])
+        m.nelem[d] = int(elems[d]) if d < len(elems) else 0
+        m.length[d] = float(lengths[d]) if d < len(lengths) else 1.0
     for f, comps in (clamp or {}).items():
         bits = 0
         for c in comps:

@@ -660,13 +660,17 @@ sdme_status sdme_create(sdme_ctx** out, const sdme_mesh_desc* mesh, const sdme_m
   *out = nullptr;
   if (check_basis(basis) != SDME_OK) return SDME_EINVAL;
   if (prec != SDME_FP64 && prec != SDME_MIXED_FP32) return SDME_EINVAL;
-  for (int d = 0; d < 3; ++d)
+  // nelem[2] == 0: a plane-strain mesh of quadrilaterals in the x-y plane
+  const int dim = mesh->nelem[2] == 0 ? 2 : 3;
+  for (int d = 0; d < dim; ++d)
     if (mesh->nelem[d] < 1 || !(mesh->length[d] > 0.0)) return SDME_EINVAL;
+  if (dim == 2 && (mesh->clamp[4] != 0 || mesh->clamp[5] != 0 || basis->kind == SDME_NODAL_LUMPED))
+    return SDME_EINVAL;
   if (!(mat->mu > 0.0) || !(mat->lambda >= 0.0) || !(mat->rho >= 0.0)) return SDME_EINVAL;
   const int P = basis->P, n = P + 1, Q = P + 2;
   int64_t N[3];
-  for (int d = 0; d < 3; ++d) N[d] = (int64_t)mesh->nelem[d] * P + 1;
-  const int64_t nelem = (int64_t)mesh->nelem[0] * mesh->nelem[1] * mesh->nelem[2];
+  for (int d = 0; d < 3; ++d) N[d] = (d < dim) ? (int64_t)mesh->nelem[d] * P + 1 : 1;
+  const int64_t nelem = (int64_t)mesh->nelem[0] * mesh->nelem[1] * (dim == 3 ? mesh->nelem[2] : 1);
   if (nelem > 0x7fffffff || N[0] * N[1] * N[2] * 3 > ((int64_t)1 << 40)) return SDME_EINVAL;
 
   sdme_ctx* ctx = new (std::nothrow) sdme_ctx();
@@ -709,22 +713,23 @@ sdme_status sdme_create(sdme_ctx** out, const sdme_mesh_desc* mesh, const sdme_m
     h.pairs = sym == kEoNodalPairs ? 1 : 0;
   }
   double hh[3];
+  h.dim = dim;
   for (int d = 0; d < 3; ++d) {
-    hh[d] = mesh->length[d] / mesh->nelem[d];
-    h.s[d] = 2.0 / hh[d];
-    h.ne[d] = mesh->nelem[d];
+    hh[d] = d < dim ? mesh->length[d] / mesh->nelem[d] : 2.0;
+    h.s[d] = d < dim ? 2.0 / hh[d] : 0.0;
+    h.ne[d] = d < dim ? mesh->nelem[d] : 1;
     h.N[d] = (int)N[d];
     ctx->mi.N[d] = (int)N[d];
   }
-  h.detJ = hh[0] * hh[1] * hh[2] / 8.0;
+  h.detJ = dim == 3 ? hh[0] * hh[1] * hh[2] / 8.0 : hh[0] * hh[1] / 4.0;
   h.mu = mat->mu;
   h.lam = mat->lambda;
   h.rho = mat->rho;
   h.Nn = N[0] * N[1] * N[2];
   for (int f = 0; f < 6; ++f) h.clamp[f] = ctx->mi.clamp[f] = mesh->clamp[f] & 7u;
   ctx->mi.Nn = h.Nn;
-  ctx->mi.ndof = 3 * h.Nn;
-  ctx->ndof = 3 * h.Nn;
+  ctx->mi.ndof = dim * h.Nn;
+  ctx->ndof = dim * h.Nn;
   ctx->Q = Q;
 
   // NULL is the legacy default stream, which orders with every other
@@ -829,7 +834,7 @@ sdme_status sdme_set_condensation(sdme_ctx* ctx, int enable) {
   if (ctx->cond) return SDME_OK;
   const HostElemData& h = ctx->h;
   const int P = h.P, n = P + 1, n3 = n * n * n;
-  if (ctx->prec != SDME_FP64 || ctx->mlump || P < 2 || h.nelem > 65535) return SDME_EUNSUPPORTED;
+  if (ctx->prec != SDME_FP64 || ctx->mlump || P < 2 || h.nelem > 65535 || h.dim != 3) return SDME_EUNSUPPORTED;
   const int N = 3 * n3, Ni = 3 * (n - 2) * (n - 2) * (n - 2), Nb = N - Ni;
   std::vector<int> Il, Bl;
   for (int idx = 0; idx < N; ++idx) {
@@ -895,6 +900,7 @@ sdme_status sdme_set_condensation(sdme_ctx* ctx, int enable) {
 sdme_status sdme_internal_force_vjp(sdme_ctx* ctx, const double* u_dev, const double* w_dev, double* gu_dev,
                                     double* gmu, double* glambda) {
   if (!ctx || !u_dev || !w_dev || !gu_dev) return SDME_EINVAL;
+  if (ctx->h.dim != 3) return SDME_EUNSUPPORTED;
   SDME_TRY(residual_launch(ctx, 0.0, u_dev, ctx->y));
   SDME_CUDA(cudaMemsetAsync(gu_dev, 0, sizeof(double) * ctx->ndof, ctx->stream));
   SDME_CUDA(dispatch_P(ctx->h.P, [&](auto Pc) {
@@ -958,6 +964,28 @@ sdme_status sdme_traction_load(sdme_ctx* ctx, int face, const double t[3], doubl
   if (!ctx || !t || !f_dev || face < 0 || face > 5) return SDME_EINVAL;
   const HostElemData& h = ctx->h;
   const int P = h.P, n = P + 1, Q = ctx->Q;
+  if (h.dim == 2) {
+    // dead traction (t[0], t[1]) on one edge of the rectangle (per unit out-of-plane length)
+    if (face > 3) return SDME_EINVAL;
+    std::vector<double> I(n, 0.0);
+    for (int q = 0; q < Q; ++q)
+      for (int j = 0; j < n; ++j) I[j] += h.W[q] * h.B[q * n + j];
+    const int axis = face / 2, side = face % 2, tang = 1 - axis;
+    const double jac = 0.5 * ctx->mesh.length[tang] / ctx->mesh.nelem[tang];
+    const int fixed = side ? h.N[axis] - 1 : 0;
+    std::vector<double> f(ctx->ndof, 0.0);
+    for (int et = 0; et < h.ne[tang]; ++et)
+      for (int a = 0; a < n; ++a) {
+        int idx[2];
+        idx[axis] = fixed;
+        idx[tang] = et * P + a;
+        const int64_t node = (int64_t)idx[1] * h.N[0] + idx[0];
+        for (int c = 0; c < 2; ++c) f[c * h.Nn + node] += t[c] * jac * I[a];
+      }
+    SDME_CUDA(cudaMemcpyAsync(f_dev, f.data(), sizeof(double) * ctx->ndof, cudaMemcpyHostToDevice, ctx->stream));
+    SDME_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SDME_OK;
+  }
   // 1D integrals I_j = int_{-1}^{1} phi_j
   std::vector<double> I(n, 0.0);
   for (int q = 0; q < Q; ++q)
@@ -1144,6 +1172,7 @@ sdme_status sdme_estimate_dt_crit(sdme_ctx* ctx, const double* u_dev, int iters,
 }
 
 sdme_status sdme_body_load(sdme_ctx* ctx, const double* fq_dev, double* f_dev) {
+  if (ctx && ctx->h.dim != 3) return SDME_EUNSUPPORTED;
   if (!ctx || !fq_dev || !f_dev) return SDME_EINVAL;
   SDME_CUDA(cudaMemsetAsync(f_dev, 0, sizeof(double) * ctx->ndof, ctx->stream));
   SDME_CUDA(dispatch_P(ctx->h.P, [&](auto Pc) {
@@ -1191,6 +1220,7 @@ sdme_status sdme_get_timing(sdme_ctx* ctx, sdme_timing* out) {
 
 sdme_status sdme_tape_create(sdme_ctx* ctx, int nsteps, int every, sdme_tape** out) {
   if (!ctx || !out || nsteps < 1 || every < 1) return SDME_EINVAL;
+  if (ctx->h.dim != 3) return SDME_EUNSUPPORTED;
   *out = nullptr;
   sdme_tape* tp = new (std::nothrow) sdme_tape();
   if (!tp) return SDME_ENOMEM;

@@ -7,6 +7,23 @@
 
 namespace sdme {
 
+// plane-strain quadrilateral launchers (quad_launch.cuh), used for 2D meshes
+template <int P>
+cudaError_t launch_quad_residual(const HostElemData& h, double b1, const double* u, double* y, double* st64,
+                                 float* st32, int* err, cudaStream_t s);
+template <int P, typename T, typename TV, bool STIFF>
+cudaError_t launch_quad_tangent(const HostElemData& h, double b1, const TV* x, TV* y, const T* st, double* partial,
+                                PcgScalars* scal, cudaStream_t s);
+template <int P, typename T>
+cudaError_t launch_quad_diag(const HostElemData& h, double b1, const T* st, T* y, cudaStream_t s);
+template <int P>
+cudaError_t launch_quad_mass(const HostElemData& h, const double* x, double* y, cudaStream_t s);
+template <int P, typename T>
+cudaError_t launch_quad_mass_diag(const HostElemData& h, double b1, T* y, cudaStream_t s);
+template <int P>
+cudaError_t launch_quad_energy(const HostElemData& h, const double* u, double* partial, unsigned int* counter,
+                               double* out, int* err, cudaStream_t s);
+
 template <typename T, int P>
 static ElemParams<T, P> make_params(const HostElemData& h, double b1) {
   ElemParams<T, P> p;
@@ -65,6 +82,7 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 template <int P>
 cudaError_t launch_residual(const HostElemData& h, double b1, const double* u, double* y, double* st64,
                             float* st32, int* err, cudaStream_t s) {
+  if (h.dim == 2) return launch_quad_residual<P>(h, b1, u, y, st64, st32, err, s);
   static bool init = false;
   const size_t smem = sizeof(double) * elem_smem_words<P>();
   if (!init) {
@@ -80,6 +98,7 @@ cudaError_t launch_residual(const HostElemData& h, double b1, const double* u, d
 template <int P, typename T, typename TV>
 cudaError_t launch_tangent(const HostElemData& h, double b1, const TV* x, TV* y, const T* st,
                            double* partial, PcgScalars* scal, cudaStream_t s) {
+  if (h.dim == 2) return launch_quad_tangent<P, T, TV, true>(h, b1, x, y, st, partial, scal, s);
   static bool init = false;
   const size_t smem = sizeof(T) * elem_smem_words<P>();
   if (!init) {
@@ -94,6 +113,7 @@ cudaError_t launch_tangent(const HostElemData& h, double b1, const TV* x, TV* y,
 
 template <int P, typename T>
 cudaError_t launch_diag(const HostElemData& h, double b1, const T* st, T* y, cudaStream_t s) {
+  if (h.dim == 2) return launch_quad_diag<P, T>(h, b1, st, y, s);
   static bool init = false;
   const size_t smem = sizeof(T) * diag_smem_words<P>();
   if (!init) {
@@ -108,6 +128,7 @@ cudaError_t launch_diag(const HostElemData& h, double b1, const T* st, T* y, cud
 
 template <int P>
 cudaError_t launch_mass(const HostElemData& h, const double* x, double* y, cudaStream_t s) {
+  if (h.dim == 2) return launch_quad_mass<P>(h, x, y, s);
   static bool init = false;
   const size_t smem = sizeof(double) * elem_smem_words<P>();
   if (!init) {
@@ -123,6 +144,7 @@ cudaError_t launch_mass(const HostElemData& h, const double* x, double* y, cudaS
 template <int P, typename T, typename TV>
 cudaError_t launch_mass_op(const HostElemData& h, double b1, const TV* x, TV* y, double* partial, PcgScalars* scal,
                            cudaStream_t s) {
+  if (h.dim == 2) return launch_quad_tangent<P, T, TV, false>(h, b1, x, y, nullptr, partial, scal, s);
   static bool init = false;
   // the mass-only operator never touches the fourth shared field (Gz)
   const size_t smem = sizeof(T) * 9 * Geo<P>::FQ;
@@ -138,6 +160,7 @@ cudaError_t launch_mass_op(const HostElemData& h, double b1, const TV* x, TV* y,
 
 template <int P, typename T>
 cudaError_t launch_mass_diag(const HostElemData& h, double b1, T* y, cudaStream_t s) {
+  if (h.dim == 2) return launch_quad_mass_diag<P, T>(h, b1, y, s);
   auto prm = make_params<T, P>(h, b1);
   mass_diag_kernel<P, T><<<h.nelem, 256, 0, s>>>(prm, y);
   return cudaGetLastError();
@@ -146,6 +169,7 @@ cudaError_t launch_mass_diag(const HostElemData& h, double b1, T* y, cudaStream_
 template <int P>
 cudaError_t launch_energy(const HostElemData& h, const double* u, double* partial, unsigned int* counter,
                           double* out, int* err, cudaStream_t s) {
+  if (h.dim == 2) return launch_quad_energy<P>(h, u, partial, counter, out, err, s);
   static bool init = false;
   const size_t smem = sizeof(double) * elem_smem_words<P>();
   if (!init) {
@@ -160,6 +184,7 @@ cudaError_t launch_energy(const HostElemData& h, const double* u, double* partia
 
 template <int P>
 cudaError_t launch_body_load(const HostElemData& h, const double* fq, double* y, cudaStream_t s) {
+  if (h.dim == 2) return cudaErrorNotSupported;
   static bool init = false;
   const size_t smem = sizeof(double) * elem_smem_words<P>();
   if (!init) {

@@ -14,6 +14,7 @@ struct PcgScalars;
 // converts it into its kernel-parameter block.
 struct HostElemData {
   int P = 0;
+  int dim = 3;                       // 3: hexahedra; 2: plane-strain quadrilaterals (ne[2] = N[2] = 1)
   int nelem = 0;
   std::vector<double> B, D, DQ, W;   // Q x n, Q x n, Q x Q, Q (lattice order)
   // even-odd half tables (eo_tables.h) and the nodal-pairing flag

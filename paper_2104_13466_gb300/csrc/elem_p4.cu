@@ -2,6 +2,7 @@
 #include "batch_elem.cuh"
 #include "cond_columns.cuh"
 #include "elem_adjoint.cuh"
+#include "quad_launch.cuh"
 
 namespace sdme {
 SDME_INSTANTIATE_ORDER(4)
