@@ -164,6 +164,23 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(ms, device):
+    """The slowest rank's time (replicas: the job ends when the last one does);
+    the local time when no process group is initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(ws, ndof, matvecs, ms):
+    """Whole-job DOF/s of ws identical replicas timed to the slowest one."""
+    return ws * ndof * matvecs / (ms * 1e-3)
+
+
 def cpu_oracle_matvec(w, basis, nsample, seed=0):
     """The FP64 oracle's tangent action on a bounded sample of elements of
     the same mesh; returns (DOF/s scaled to the whole mesh, seconds, cores)."""
@@ -267,13 +284,9 @@ def run_gpu(args, w):
         torch.cuda.synchronize()
     ctx.set_timing(False)
     t1 = ctx.timing()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
     matvecs = sum(s["matvecs"] for s in stats)
-    value = ws * n * matvecs / (ms * 1e-3)
+    value = replica_throughput(ws, n, matvecs, ms)
     tan_ms = (t1["tangent_ms"] - t0["tangent_ms"])
     tan_launches = t1["tangent_launches"] - t0["tangent_launches"]
     avg_tan = tan_ms / max(1, tan_launches)
