@@ -163,3 +163,36 @@ def test_batch_rejects_invalid_problems():
     bad[1]["P"] = 9
     with pytest.raises(s.SdmeError):
         _batch(bad, "sdme_h")
+
+
+def test_batch_single_problem_and_idle_problems():
+    # one problem alone, and a batch where some problems carry no load: those
+    # converge at Newton iteration 0 while the others iterate
+    probs = _problems(seed=4, n=4, orders=(2, 3), max_e=2)
+    one = _batch(probs[:1], "sdme_h")
+    ds = _oracles(probs[:1], "sdme_h")
+    u = _random_state(one, ds, 0.05, 40)
+    R = one.zeros()
+    one.internal_force(_dev(u), R)
+    assert _rel(_host(R)[:one.ndofs[0]], ds[0].internal_force(u[:one.ndofs[0]])) < TOL64
+    b = _batch(probs, "sdme_m")
+    f = b.zeros()
+    b.traction_load("zmax", [(0.0, 0.0, -5.0 if i % 2 else 0.0) for i in range(b.nprob)], f)
+    u, v, a = b.zeros(), b.zeros(), b.zeros()
+    stats = b.newmark_step(u, v, a, 0.01, f, newton_tol=1e-10)
+    for i, st in enumerate(stats):
+        assert st["converged"]
+        if i % 2 == 0:
+            assert st["newton_iters"] == 0 and st["pcg_iters_total"] == 0
+            assert float(b.segment(u, i).abs().max()) == 0.0
+        else:
+            assert st["newton_iters"] >= 1
+
+
+def test_batch_refuses_planar_meshes():
+    import paper_2104_13466_gb300 as s
+    probs = _problems(n=2)
+    probs[0]["elems"] = (2, 2)
+    probs[0]["lengths"] = (1.0, 1.0)
+    with pytest.raises(s.SdmeError):
+        _batch(probs, "sdme_h")
