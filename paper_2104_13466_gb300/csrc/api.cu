@@ -23,6 +23,10 @@ namespace {
 
 constexpr int kVecBlocks = 152 * 8;      // per-DOF grid: 8 CTAs of 256 threads per SM
 constexpr int kPcgChunk = 16;            // iterations per CUDA graph / host status read
+// Up to this many elements the PCG step length is summed by the update
+// kernel from the operator's per-element partials (every update CTA reads
+// them all) instead of by the operator's last CTA.
+constexpr int64_t kDeferMaxElems = 8192;
 
 #define SDME_CUDA(call)                                           \
   do {                                                            \
@@ -61,6 +65,12 @@ struct sdme_ctx {
   int* err = nullptr;
   PcgScalars* scal = nullptr;
   double* partial = nullptr;    // per-element / per-CTA partial sums
+  int64_t upart_off = 0;        // PCG update partials start here (after the per-element ones)
+  int* loc = nullptr;           // tangent gather / scatter offset table (3 n^3), or null
+  // grids of the PCG update / direction kernels: one resident wave each
+  // (index 0: float64 vectors, 1: float32), so the update's step-length
+  // preamble runs once per SM slot
+  int upd_blocks[2] = {kVecBlocks, kVecBlocks}, dir_blocks[2] = {kVecBlocks, kVecBlocks};
   double* dscal = nullptr;      // [0]: norm^2 results ; counters follow
   unsigned int* dcount = nullptr;
   // PCG vectors
@@ -158,14 +168,14 @@ sdme_status sync_and_check(sdme_ctx* ctx) {
 
 template <typename T, typename TV>
 sdme_status tangent_launch(sdme_ctx* ctx, double b1, const TV* x, TV* y, double* partial, PcgScalars* scal,
-                           cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
+                           cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr, bool defer = false) {
   const HostElemData& h = ctx->h;
   const T* st;
   if constexpr (sizeof(T) == 8) st = ctx->st64;
   else st = ctx->st32;
   if (e0) SDME_CUDA(cudaEventRecord(e0, ctx->stream));
   SDME_CUDA(dispatch_P(h.P, [&](auto Pc) {
-    return launch_tangent<decltype(Pc)::value, T, TV>(h, b1, x, y, st, partial, scal, ctx->stream);
+    return launch_tangent<decltype(Pc)::value, T, TV>(h, b1, x, y, st, partial, scal, ctx->stream, defer);
   }));
   if (e1) SDME_CUDA(cudaEventRecord(e1, ctx->stream));
   ctx->kernel_launches += 1;
@@ -205,6 +215,9 @@ enum PcgOp { kOpTangent = 0, kOpMass = 1, kOpCondensed = 2 };
 // Issue one chunk of PCG iterations (operator, update, direction) on ctx->stream.
 template <typename T, typename TV>
 sdme_status pcg_chunk(sdme_ctx* ctx, double b1, int op, bool tim, TV* r, TV* p, TV* q, TV* dinv, TV* xv) {
+  // hexahedral tangent / mass operators leave p.(A p) as per-element
+  // partials for the update kernel (no last-CTA finalize in the operator)
+  const bool defer = op != kOpCondensed && ctx->h.dim == 3 && ctx->h.nelem <= kDeferMaxElems;
   for (int j = 0; j < kPcgChunk; ++j) {
     if (op == kOpCondensed) {
       if constexpr (sizeof(TV) == 8) {
@@ -218,16 +231,19 @@ sdme_status pcg_chunk(sdme_ctx* ctx, double b1, int op, bool tim, TV* r, TV* p, 
       }
     } else if (op == kOpMass) {
       SDME_CUDA(dispatch_P(ctx->h.P, [&](auto Pc) {
-        return launch_mass_op<decltype(Pc)::value, T, TV>(ctx->h, b1, p, q, ctx->partial, ctx->scal, ctx->stream);
+        return launch_mass_op<decltype(Pc)::value, T, TV>(ctx->h, b1, p, q, ctx->partial, ctx->scal, ctx->stream,
+                                                          defer);
       }));
       ctx->kernel_launches += 1;
     } else {
       SDME_TRY((tangent_launch<T, TV>(ctx, b1, p, q, ctx->partial, ctx->scal, tim ? ctx->ev[2 * j] : nullptr,
-                                      tim ? ctx->ev[2 * j + 1] : nullptr)));
+                                      tim ? ctx->ev[2 * j + 1] : nullptr, defer)));
     }
-    k_pcg_update<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, xv, r, p, q, dinv, ctx->scal,
-                                                                  ctx->partial);
-    k_pcg_direction<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, r, dinv, p, ctx->scal);
+    constexpr int vi = sizeof(TV) == 4 ? 1 : 0;
+    k_pcg_update<TV><<<ctx->upd_blocks[vi], kVecThreads, 0, ctx->stream>>>(
+        ctx->ndof, xv, r, p, q, dinv, ctx->scal, ctx->partial + ctx->upart_off, defer ? ctx->partial : nullptr,
+        (int)ctx->h.nelem);
+    k_pcg_direction<TV><<<ctx->dir_blocks[vi], kVecThreads, 0, ctx->stream>>>(ctx->ndof, r, dinv, p, ctx->scal);
   }
   SDME_CUDA(cudaGetLastError());
   return SDME_OK;
@@ -463,7 +479,7 @@ void free_all(sdme_ctx* ctx) {
                  ctx->r64, ctx->p64, ctx->q64, ctx->d64, ctx->x64, ctx->r32, ctx->p32, ctx->q32, ctx->d32,
                  ctx->x32, ctx->un, ctx->ahat, ctx->mhat, ctx->y, ctx->psi, ctx->du, ctx->mlump,
                  ctx->cIl, ctx->cBl, ctx->cerr, ctx->cgI, ctx->cgB, ctx->cKe, ctx->cL, ctx->cW, ctx->cS,
-                 ctx->cY, ctx->cg};
+                 ctx->cY, ctx->cg, ctx->loc};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (ctx->scal_h) cudaFreeHost(ctx->scal_h);
@@ -738,13 +754,26 @@ sdme_status sdme_create(sdme_ctx** out, const sdme_mesh_desc* mesh, const sdme_m
   ctx->own_stream = false;
   const int64_t nst = nelem * kStateFields * (int64_t)Q * Q * Q;
   const int64_t nd = ctx->ndof;
-  const int64_t npart = std::max<int64_t>(2 * nelem, 2 * kVecBlocks) + 64;
+  ctx->upart_off = (nelem + 31) / 32 * 32;
+  const int64_t npart = std::max<int64_t>(2 * nelem, 2 * kVecBlocks) + 64 + ctx->upart_off + 2 * kVecBlocks;
   bool ok = true;
   ok = ok && dalloc(&ctx->st64, nst) == cudaSuccess;
   if (prec == SDME_MIXED_FP32) ok = ok && dalloc(&ctx->st32, nst) == cudaSuccess;
   ok = ok && dalloc(&ctx->err, 1) == cudaSuccess;
   ok = ok && dalloc(&ctx->scal, 1) == cudaSuccess;
   ok = ok && dalloc(&ctx->partial, npart) == cudaSuccess;
+  if (ok && dim == 3 && P % 2 == 0 && 3 * h.Nn <= (int64_t)INT32_MAX) {
+    // offset of entry (c, r, q, p) from the element's corner lattice point
+    std::vector<int> loc(3 * n * n * n);
+    for (int c = 0; c < 3; ++c)
+      for (int r = 0; r < n; ++r)
+        for (int q = 0; q < n; ++q)
+          for (int pp = 0; pp < n; ++pp)
+            loc[((c * n + r) * n + q) * n + pp] = (int)(c * h.Nn + ((int64_t)r * h.N[1] + q) * h.N[0] + pp);
+    ok = dalloc(&ctx->loc, (int64_t)loc.size()) == cudaSuccess &&
+         cudaMemcpy(ctx->loc, loc.data(), sizeof(int) * loc.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    h.loc = ctx->loc;
+  }
   ok = ok && dalloc(&ctx->dscal, 8) == cudaSuccess;
   ok = ok && dalloc(&ctx->dcount, 8) == cudaSuccess;
   if (prec == SDME_MIXED_FP32) {
@@ -774,6 +803,19 @@ sdme_status sdme_create(sdme_ctx** out, const sdme_mesh_desc* mesh, const sdme_m
          cudaMemsetAsync(ctx->scal, 0, sizeof(PcgScalars), ctx->stream) == cudaSuccess &&
          cudaMemsetAsync(ctx->dcount, 0, 8 * sizeof(unsigned int), ctx->stream) == cudaSuccess &&
          cudaStreamSynchronize(ctx->stream) == cudaSuccess;
+  }
+  if (ok) {
+    int dev = 0, sms = 0;
+    ok = cudaGetDevice(&dev) == cudaSuccess &&
+         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+    auto wave = [&](auto kernel, int* out) {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kVecThreads, 0) != cudaSuccess) return false;
+      *out = std::max(1, std::min(kVecBlocks, per_sm * sms));
+      return true;
+    };
+    ok = ok && wave(k_pcg_update<double>, &ctx->upd_blocks[0]) && wave(k_pcg_update<float>, &ctx->upd_blocks[1]) &&
+         wave(k_pcg_direction<double>, &ctx->dir_blocks[0]) && wave(k_pcg_direction<float>, &ctx->dir_blocks[1]);
   }
   if (ok && basis->kind == SDME_NODAL_LUMPED) ok = build_lumped_mass(ctx) == SDME_OK;
   if (!ok) {

@@ -164,4 +164,18 @@ __device__ __forceinline__ double ordered_sum(const double* part, int m) {
   return block_sum(s);
 }
 
+// Deterministic sum of m partials written by an earlier kernel, with eight
+// loads in flight per thread (fixed order for a given m and block size).
+__device__ __forceinline__ double ordered_sum_prev(const double* __restrict__ part, int m) {
+  const int bd = blockDim.x;
+  double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int i = threadIdx.x;
+  for (; i + 7 * bd < m; i += 8 * bd) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] += __ldcg(part + i + k * bd);
+  }
+  for (; i < m; i += bd) a[0] += __ldcg(part + i);
+  return block_sum(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
+}
+
 }  // namespace sdme

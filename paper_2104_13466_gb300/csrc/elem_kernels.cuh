@@ -66,6 +66,11 @@ template <typename T, int P>
 struct ElemParams : MeshParams<T> {
   ElemTables<T, P> tab;
   int pairs;     // 1: nodal basis, pair mirrored internal nodes on the fly
+  // Optional (device, 3 n^3 ints): lattice offset of entry (c, r, q, p)
+  // relative to the element's corner, c Nn + (r N1 + q) N0 + p.  The same
+  // for every element, so the tangent gather / scatter of elements away
+  // from clamped faces is one table read and one add per entry.
+  const int* loc = nullptr;
 };
 
 //-----------------------------------------------------------------------------
@@ -659,9 +664,16 @@ constexpr int tangent_min_blocks() {
 // shared layout): forward stages, pointwise linearised stress (and the fused
 // mass term), transposed stages; the result replaces X.
 template <int P, typename T, bool STIFF>
-__device__ __forceinline__ void tangent_core(const ElemTables<T, P>& tb, int pairs, const MeshParams<T>& m, int e,
-                                             const T* __restrict__ st, T* sm) {
+__device__ __forceinline__ T tangent_core(const ElemTables<T, P>& tb, int pairs, const MeshParams<T>& m, int e,
+                                          const T* __restrict__ st, T* sm) {
   using G = Geo<P>;
+  // float32: returns this thread's share of x_e . (K_e x_e).  The
+  // transposed stages are the exact adjoint of the forward ones, so the
+  // element product equals the quadrature form
+  // sum_q w_q (dF : dP + b1 rho |x(q)|^2), summed here at no memory cost.
+  // float64 (bound by the float64 pipe) returns 0; its caller re-reads x.
+  constexpr bool QDOT = sizeof(T) == 4;
+  T dotq = T(0);
   constexpr int Q = P + 2, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
   constexpr int NT = G::NT;
   forward_stages<T, P, STIFF>(tb, pairs, sm);
@@ -673,7 +685,11 @@ __device__ __forceinline__ void tangent_core(const ElemTables<T, P>& tb, int pai
       const int so = (qz * Q + qy) * XQ + qx;
       const T mfac = m.b1 * m.rho * tb.W[qx] * tb.W[qy] * tb.W[qz] * m.detJ;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= mfac;
+      for (int c = 0; c < 3; ++c) {
+        const T u = sm[c * FQ + so];
+        sm[c * FQ + so] = u * mfac;
+        if (QDOT) dotq += mfac * u * u;
+      }
     }
   }
   for (int q = threadIdx.x; STIFF && q < Q3; q += NT) {
@@ -701,6 +717,7 @@ __device__ __forceinline__ void tangent_core(const ElemTables<T, P>& tb, int pai
       for (int j = 0; j < 3; ++j) W[a][j] = dF[0][a] * H[0][j] + dF[1][a] * H[1][j] + dF[2][a] * H[2][j];
     const T wdet = tb.W[qx] * tb.W[qy] * tb.W[qz] * m.detJ;
     const T ltr = m.lam * tr;
+    T qf = T(0);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -708,59 +725,93 @@ __device__ __forceinline__ void tangent_core(const ElemTables<T, P>& tb, int pai
         const T V = H[i][0] * W[0][j] + H[i][1] * W[1][j] + H[i][2] * W[2][j];
         const T dP = m.mu * dF[i][j] + cst * V + ltr * H[i][j];
         sm[(3 + 3 * j + i) * FQ + so] = wdet * dP * sc[j];
+        if (QDOT) qf += dF[i][j] * dP;
       }
     const T mfac = m.b1 * m.rho * wdet;
+    T mq = T(0);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= mfac;
+    for (int c = 0; c < 3; ++c) {
+      const T u = sm[c * FQ + so];
+      sm[c * FQ + so] = u * mfac;
+      if (QDOT) mq += u * u;
+    }
+    if (QDOT) dotq += wdet * qf + mfac * mq;
   }
   __syncthreads();
   transpose_stages<T, P, STIFF>(tb, pairs, sm);
+  return dotq;
 }
 
 template <int P, typename T, typename TV, bool STIFF>
 __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pairs, const MeshParams<T>& m, int e,
                                              const TV* __restrict__ x, TV* __restrict__ y,
                                              const T* __restrict__ st, double* __restrict__ dot_partial,
-                                             unsigned nparts, PcgScalars* __restrict__ scal, T* sm) {
+                                             unsigned nparts, PcgScalars* __restrict__ scal, T* sm,
+                                             const int* __restrict__ loc = nullptr, bool defer = false) {
   using G = Geo<P>;
-  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, FQ = G::FQ;
+  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q;
   constexpr int NT = G::NT;  // == blockDim.x: compile-time strides let the loops batch their loads
-  if (scal && scal->status != 0) return;
+  // the solver's status word is read now and tested after the gather, so
+  // its latency overlaps the gather's loads (nothing is written before)
+  const int stat0 = scal ? *reinterpret_cast<volatile const int*>(&scal->status) : 0;
   if constexpr (STIFF) {
     // start pulling the element's linearisation state into L2 now; the
     // pointwise stage reads it after the gather and the forward stages
     if (threadIdx.x == 0) prefetch_l2(st + (int64_t)e * kStateFields * Q3, sizeof(T) * kStateFields * Q3);
   }
-  T* X = sm + 3 * FQ;
+  T* X = sm + 3 * G::FQ;
   const ElemView<MeshParams<T>> view(m, P, e);
+  // fast path: an element off every clamped face with the offset table;
+  // X is [3][n][n][n] unpadded for even P (odd n), so its offset is idx
+  const bool fast = (G::XN == n) && loc != nullptr && !view.boundary;
+  if (fast) {
+    const TV* xb = x + view.base;
 #pragma unroll
-  for (int idx = threadIdx.x; idx < 3 * n3; idx += NT) {
-    bool cons;
-    int so;
-    const int64_t g = entry_index<P>(m, view, idx, &cons, &so);
-    X[so] = cons ? T(0) : (T)x[g];
+    for (int idx = threadIdx.x; idx < 3 * n3; idx += NT) X[idx] = (T)xb[__ldg(loc + idx)];
+  } else {
+#pragma unroll
+    for (int idx = threadIdx.x; idx < 3 * n3; idx += NT) {
+      bool cons;
+      int so;
+      const int64_t g = entry_index<P>(m, view, idx, &cons, &so);
+      X[so] = cons ? T(0) : (T)x[g];
+    }
   }
   __syncthreads();
-  tangent_core<P, T, STIFF>(tb, pairs, m, e, st, sm);
-  T dotT = T(0);
+  if (stat0 != 0) return;
+  T dotT = tangent_core<P, T, STIFF>(tb, pairs, m, e, st, sm);
+  constexpr bool RELOAD = sizeof(T) == 8;  // float64: x_e . y_e from a second read of x
+  if (fast) {
+    const TV* xb = x + view.base;
+    TV* yb = y + view.base;
 #pragma unroll
-  for (int idx = threadIdx.x; idx < 3 * n3; idx += NT) {
-    bool cons;
-    int so;
-    const int64_t g = entry_index<P>(m, view, idx, &cons, &so);
-    if (!cons) {
-      const T v = X[so];
-      atomicAdd(&y[g], (TV)v);
-      if (dot_partial) dotT += v * (T)x[g];
+    for (int idx = threadIdx.x; idx < 3 * n3; idx += NT) {
+      const int o = __ldg(loc + idx);
+      const T v = X[idx];
+      atomicAdd(&yb[o], (TV)v);
+      if (RELOAD && dot_partial) dotT += v * (T)xb[o];
+    }
+  } else {
+#pragma unroll
+    for (int idx = threadIdx.x; idx < 3 * n3; idx += NT) {
+      bool cons;
+      int so;
+      const int64_t g = entry_index<P>(m, view, idx, &cons, &so);
+      if (!cons) {
+        const T v = X[so];
+        atomicAdd(&y[g], (TV)v);
+        if (RELOAD && dot_partial) dotT += v * (T)x[g];
+      }
     }
   }
   if (dot_partial) {
     // x_e . (K_e x_e) summed over elements gives x . (K x) for the PCG step
-    // length; summed in T within the CTA, float64 across CTAs with a
-    // fixed-order (deterministic) finalize by the last CTA to finish.
+    // length (x_e is zero on constrained entries); summed in T within the
+    // CTA, float64 across CTAs in a fixed order: by the last CTA to finish
+    // here, or (defer) by every CTA of the following PCG update.
     const double tot = static_cast<double>(block_sum_t(dotT));
     if (threadIdx.x == 0) dot_partial[e] = tot;
-    if (scal && last_arrival(&scal->counter, nparts)) {
+    if (scal && !defer && last_arrival(&scal->counter, nparts)) {
       const double pq = ordered_sum(dot_partial, (int)nparts);
       if (threadIdx.x == 0) {
         scal->pq = pq;
@@ -776,10 +827,10 @@ template <int P, typename T, typename TV, bool STIFF = true>
 __global__ void __launch_bounds__(elem_threads(P), tangent_min_blocks<T>())
 tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restrict__ x,
                TV* __restrict__ y, const T* __restrict__ st, double* __restrict__ dot_partial,
-               PcgScalars* __restrict__ scal) {
+               PcgScalars* __restrict__ scal, int defer = 0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   tangent_body<P, T, TV, STIFF>(prm.tab, prm.pairs, prm, blockIdx.x, x, y, st, dot_partial, gridDim.x, scal,
-                                reinterpret_cast<T*>(smem_raw));
+                                reinterpret_cast<T*>(smem_raw), prm.loc, defer != 0);
 }
 
 //-----------------------------------------------------------------------------

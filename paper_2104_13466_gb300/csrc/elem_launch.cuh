@@ -56,6 +56,7 @@ static ElemParams<T, P> make_params(const HostElemData& h, double b1) {
     }
   }
   p.pairs = h.pairs;
+  p.loc = h.loc;
   for (int d = 0; d < 3; ++d) {
     p.s[d] = (T)h.s[d];
     p.ne[d] = h.ne[d];
@@ -97,7 +98,7 @@ cudaError_t launch_residual(const HostElemData& h, double b1, const double* u, d
 
 template <int P, typename T, typename TV>
 cudaError_t launch_tangent(const HostElemData& h, double b1, const TV* x, TV* y, const T* st,
-                           double* partial, PcgScalars* scal, cudaStream_t s) {
+                           double* partial, PcgScalars* scal, cudaStream_t s, bool defer) {
   if (h.dim == 2) return launch_quad_tangent<P, T, TV, true>(h, b1, x, y, st, partial, scal, s);
   static bool init = false;
   const size_t smem = sizeof(T) * elem_smem_words<P>();
@@ -107,7 +108,7 @@ cudaError_t launch_tangent(const HostElemData& h, double b1, const TV* x, TV* y,
     init = true;
   }
   auto prm = make_params<T, P>(h, b1);
-  tangent_kernel<P, T, TV><<<h.nelem, elem_threads(P), smem, s>>>(prm, x, y, st, partial, scal);
+  tangent_kernel<P, T, TV><<<h.nelem, elem_threads(P), smem, s>>>(prm, x, y, st, partial, scal, defer ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -143,7 +144,7 @@ cudaError_t launch_mass(const HostElemData& h, const double* x, double* y, cudaS
 
 template <int P, typename T, typename TV>
 cudaError_t launch_mass_op(const HostElemData& h, double b1, const TV* x, TV* y, double* partial, PcgScalars* scal,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool defer) {
   if (h.dim == 2) return launch_quad_tangent<P, T, TV, false>(h, b1, x, y, nullptr, partial, scal, s);
   static bool init = false;
   // the mass-only operator never touches the fourth shared field (Gz)
@@ -154,7 +155,8 @@ cudaError_t launch_mass_op(const HostElemData& h, double b1, const TV* x, TV* y,
     init = true;
   }
   auto prm = make_params<T, P>(h, b1);
-  tangent_kernel<P, T, TV, false><<<h.nelem, elem_threads(P), smem, s>>>(prm, x, y, nullptr, partial, scal);
+  tangent_kernel<P, T, TV, false><<<h.nelem, elem_threads(P), smem, s>>>(prm, x, y, nullptr, partial, scal,
+                                                                          defer ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -202,22 +204,22 @@ cudaError_t launch_body_load(const HostElemData& h, const double* fq, double* y,
                                           float*, int*, cudaStream_t);                                \
   template cudaError_t launch_tangent<P, double, double>(const HostElemData&, double, const double*,   \
                                                          double*, const double*, double*, PcgScalars*, \
-                                                         cudaStream_t);                               \
+                                                         cudaStream_t, bool);                         \
   template cudaError_t launch_tangent<P, float, double>(const HostElemData&, double, const double*,    \
                                                         double*, const float*, double*, PcgScalars*,   \
-                                                        cudaStream_t);                                \
+                                                        cudaStream_t, bool);                          \
   template cudaError_t launch_tangent<P, float, float>(const HostElemData&, double, const float*,      \
                                                        float*, const float*, double*, PcgScalars*,     \
-                                                       cudaStream_t);                                 \
+                                                       cudaStream_t, bool);                           \
   template cudaError_t launch_diag<P, double>(const HostElemData&, double, const double*, double*,     \
                                               cudaStream_t);                                          \
   template cudaError_t launch_diag<P, float>(const HostElemData&, double, const float*, float*,        \
                                              cudaStream_t);                                           \
   template cudaError_t launch_mass<P>(const HostElemData&, const double*, double*, cudaStream_t);           \
   template cudaError_t launch_mass_op<P, double, double>(const HostElemData&, double, const double*, double*, \
-                                                         double*, PcgScalars*, cudaStream_t);              \
+                                                         double*, PcgScalars*, cudaStream_t, bool);        \
   template cudaError_t launch_mass_op<P, float, float>(const HostElemData&, double, const float*, float*,    \
-                                                       double*, PcgScalars*, cudaStream_t);                \
+                                                       double*, PcgScalars*, cudaStream_t, bool);          \
   template cudaError_t launch_mass_diag<P, double>(const HostElemData&, double, double*, cudaStream_t);      \
   template cudaError_t launch_mass_diag<P, float>(const HostElemData&, double, float*, cudaStream_t);        \
   template cudaError_t launch_energy<P>(const HostElemData&, const double*, double*, unsigned int*, double*, \

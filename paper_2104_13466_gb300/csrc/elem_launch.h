@@ -27,6 +27,7 @@ struct HostElemData {
   int N[3] = {0, 0, 0};
   int64_t Nn = 0;
   unsigned clamp[6] = {0, 0, 0, 0, 0, 0};
+  const int* loc = nullptr;          // device offset table of the tangent gather / scatter (or null)
 };
 
 // Per-problem scalars of a batched launch (float64 on the host).
@@ -70,14 +71,14 @@ cudaError_t launch_residual(const HostElemData& h, double b1, const double* u, d
                             float* st32, int* err, cudaStream_t s);
 template <int P, typename T, typename TV>
 cudaError_t launch_tangent(const HostElemData& h, double b1, const TV* x, TV* y, const T* st,
-                           double* partial, PcgScalars* scal, cudaStream_t s);
+                           double* partial, PcgScalars* scal, cudaStream_t s, bool defer = false);
 template <int P, typename T>
 cudaError_t launch_diag(const HostElemData& h, double b1, const T* st, T* y, cudaStream_t s);
 template <int P>
 cudaError_t launch_mass(const HostElemData& h, const double* x, double* y, cudaStream_t s);
 template <int P, typename T, typename TV>
 cudaError_t launch_mass_op(const HostElemData& h, double b1, const TV* x, TV* y, double* partial, PcgScalars* scal,
-                           cudaStream_t s);
+                           cudaStream_t s, bool defer = false);
 template <int P, typename T>
 cudaError_t launch_mass_diag(const HostElemData& h, double b1, T* y, cudaStream_t s);
 template <int P>

@@ -189,11 +189,30 @@ template <typename TV>
 __global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TV* __restrict__ x, TV* __restrict__ r,
                                                             const TV* __restrict__ p, TV* __restrict__ q,
                                                             const TV* __restrict__ dinv, PcgScalars* scal,
-                                                            double* __restrict__ partial) {
+                                                            double* __restrict__ partial,
+                                                            const double* __restrict__ dot_partial = nullptr,
+                                                            int nparts = 0) {
   if (scal->status != kPcgRunning) return;
   using V = typename Vec16<TV>::type;
   constexpr int W = Vec16<TV>::width;
-  const TV alpha = (TV)scal->alpha;
+  double alpha_d;
+  if (dot_partial) {
+    // p . (A p) from the operator's per-element partials (which must not
+    // alias `partial`), summed by every CTA in the same fixed order so that
+    // all CTAs hold the same step length; CTA 0 publishes it
+    const double pq = ordered_sum_prev(dot_partial, nparts);
+    alpha_d = scal->rz / pq;
+    const bool bad = !(pq > 0.0) || !isfinite(alpha_d);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      scal->pq = pq;
+      scal->alpha = alpha_d;
+      if (bad) scal->status = kPcgBreakdown;
+    }
+    if (bad) return;  // every CTA takes the same branch; none reaches the counter
+  } else {
+    alpha_d = scal->alpha;
+  }
+  const TV alpha = (TV)alpha_d;
   TV srz = TV(0), srr = TV(0);
   const int64_t nv = n / W;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
