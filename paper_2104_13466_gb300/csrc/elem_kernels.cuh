@@ -116,6 +116,11 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
 }
 
+// Hint that the cache line holding p be fetched into L2.
+__device__ __forceinline__ void prefetch_line_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Packed float32 multiply-add on a register pair: acc = t * v + acc, lane-wise.
 __device__ __forceinline__ void ffma2(float& ax, float& ay, float tx, float ty, float vx, float vy) {
   asm("{\n\t.reg .b64 pa, pb, pc;\n\t"
@@ -765,6 +770,12 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
   // X is [3][n][n][n] unpadded for even P (odd n), so its offset is idx
   const bool fast = (G::XN == n) && loc != nullptr && !view.boundary;
   if (fast) {
+    // the scatter's target lines, fetched into L2 while the element computes
+    if (threadIdx.x < 3 * n * n) {
+      const TV* yl = y + view.base + __ldg(loc + threadIdx.x * n);
+      prefetch_line_l2(yl);
+      prefetch_line_l2(yl + n - 1);
+    }
     const TV* xb = x + view.base;
 #pragma unroll
     for (int idx = threadIdx.x; idx < 3 * n3; idx += NT) X[idx] = (T)xb[__ldg(loc + idx)];
