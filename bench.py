@@ -727,6 +727,8 @@ def main():
         args.workload = "batch_cubes"
     if args.adjoint and args.workload == "beam_p8":
         args.workload = "beam_p6_adjoint"
+    if args.explicit and args.workload == "beam_p8":
+        args.workload = "cube_p6_explicit"
     w = workload(args.workload)
     if args.batch:
         run_batch(args, w)
