@@ -168,6 +168,34 @@ def test_pcg_mixed_reaches_float32_tolerance():
     assert np.linalg.norm(r) < 1e-4 * np.linalg.norm(bm)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pcg_above_the_deferred_size(prec):
+    # 9,216 elements: above the size up to which the PCG update sums the
+    # operator's per-element p.(A p) partials, so here the operator's last CTA
+    # forms the step length (with the table-driven gather of even orders);
+    # the true residual is checked on sampled DOFs, element by element
+    s = _sdme()
+    ctx, disc = _pair(elems=(24, 24, 16), lengths=(1.0, 1.0, 0.7), clamp={"zmin": (0, 1, 2)}, P=2,
+                      kind="sdme_h", prec=s.MIXED_FP32 if prec else 0)
+    assert disc.mesh.nelem > 8192
+    n = disc.mesh.ndof
+    b = random_vector(n, 81)
+    b1 = 100.0
+    rtol = 1e-5 if prec else 1e-10
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    its, rel = ctx.pcg_solve(_dev(np.zeros(n)), b1, _dev(b), x, rtol=rtol, maxit=20000)
+    assert rel <= rtol and its > 10
+    xh = _host(x)
+    bm = np.where(disc.mask, 0.0, b)
+    dofs = np.sort(np.random.default_rng(82).choice(np.flatnonzero(~disc.mask), 64, replace=False))
+    els = elements_touching(disc.mesh, dofs)
+    xm = np.where(disc.mask, 0.0, xh)
+    Ue, Xe = disc.gather(np.zeros(n), els), disc.gather(xm, els)
+    Ye = disc.ref.tangent_action(Ue, Xe, disc.mu, disc.lam) + b1 * disc.ref.mass_action(Xe, disc.rho)
+    r = bm[dofs] - disc.scatter(Ye, els)[dofs]
+    assert np.abs(r).max() <= (1e-4 if prec else 1e-8) * np.linalg.norm(bm)
+
+
 def _newmark_pair(prec, kind="sdme_h", steps=3):
     s = _sdme()
     w = workload("cube_p4")
