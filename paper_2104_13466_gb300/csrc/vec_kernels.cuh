@@ -195,6 +195,20 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TV* __res
   if (scal->status != kPcgRunning) return;
   using V = typename Vec16<TV>::type;
   constexpr int W = Vec16<TV>::width;
+  const int64_t nv = n / W;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // the first chunk's loads do not depend on the step length: issue them
+  // before it is summed so that their latency overlaps the sum
+  V x0, r0, p0, q0, d0;
+  const bool first = t0 < nv;
+  if (first) {
+    x0 = reinterpret_cast<const V*>(x)[t0];
+    r0 = reinterpret_cast<const V*>(r)[t0];
+    p0 = reinterpret_cast<const V*>(p)[t0];
+    q0 = reinterpret_cast<const V*>(q)[t0];
+    d0 = reinterpret_cast<const V*>(dinv)[t0];
+  }
   double alpha_d;
   if (dot_partial) {
     // p . (A p) from the operator's per-element partials (which must not
@@ -214,15 +228,7 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TV* __res
   }
   const TV alpha = (TV)alpha_d;
   TV srz = TV(0), srr = TV(0);
-  const int64_t nv = n / W;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (int64_t g = t0; g < nv; g += stride) {
-    V xv = reinterpret_cast<const V*>(x)[g];
-    V rv = reinterpret_cast<const V*>(r)[g];
-    V pv = reinterpret_cast<const V*>(p)[g];
-    V qv = reinterpret_cast<const V*>(q)[g];
-    V dv = reinterpret_cast<const V*>(dinv)[g];
+  auto body = [&](V& xv, V& rv, V& pv, V& qv, V& dv, int64_t g) {
 #pragma unroll
     for (int i = 0; i < W; ++i) {
       lane(xv, i) += alpha * lane(pv, i);
@@ -234,6 +240,34 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TV* __res
     reinterpret_cast<V*>(x)[g] = xv;
     reinterpret_cast<V*>(r)[g] = rv;
     reinterpret_cast<V*>(q)[g] = V{};
+  };
+  int64_t g = t0;
+  if (first) {
+    body(x0, r0, p0, q0, d0, t0);
+    g += stride;
+  }
+  // two chunks per trip (ten 16-byte loads in flight per thread), same
+  // chunk order as a one-chunk loop
+  for (; g + stride < nv; g += 2 * stride) {
+    V xv[2], rv[2], pv[2], qv[2], dv[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      xv[u] = reinterpret_cast<const V*>(x)[g + u * stride];
+      rv[u] = reinterpret_cast<const V*>(r)[g + u * stride];
+      pv[u] = reinterpret_cast<const V*>(p)[g + u * stride];
+      qv[u] = reinterpret_cast<const V*>(q)[g + u * stride];
+      dv[u] = reinterpret_cast<const V*>(dinv)[g + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) body(xv[u], rv[u], pv[u], qv[u], dv[u], g + u * stride);
+  }
+  for (; g < nv; g += stride) {
+    V xv = reinterpret_cast<const V*>(x)[g];
+    V rv = reinterpret_cast<const V*>(r)[g];
+    V pv = reinterpret_cast<const V*>(p)[g];
+    V qv = reinterpret_cast<const V*>(q)[g];
+    V dv = reinterpret_cast<const V*>(dinv)[g];
+    body(xv, rv, pv, qv, dv, g);
   }
   for (int64_t g = nv * W + t0; g < n; g += stride) {  // tail
     const TV qv = q[g];
