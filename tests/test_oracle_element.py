@@ -5,6 +5,7 @@ import pytest
 from oracle.assembly import Discretization
 from oracle.basis1d import KINDS, Basis1D
 from oracle.hexmesh import BoxMesh
+from oracle import material
 from oracle.material import lame
 from synthetic import random_vector
 
@@ -85,3 +86,29 @@ def test_dof_counts_static_table():
     for P, want in ((2, 300), (4, 1944), (6, 6084), (8, 13872)):
         m = BoxMesh(2, 2, 2, P).clamp("xmin")
         assert int((~m.constrained()).sum()) == want
+
+
+@pytest.mark.parametrize("kind,P", [("sdme_h", 4), ("nodal", 3), ("modal", 2)])
+def test_element_quadratic_form_equals_gauss_point_sum(kind, P):
+    # x_e . ((K_T(u) + b1 M) x)_e of one element equals the Gauss-point sum
+    # sum_q w_q (grad x : A grad x + b1 rho |x(q)|^2): the divergence and the
+    # projection are the weighted adjoints of the gradient and the values.
+    # The float32 tangent kernel takes p.(A p) for the PCG step length in this
+    # form instead of re-reading p after the scatter.
+    d = _disc(kind, P=P, elems=(2, 1, 1), lengths=(1.0, 0.8, 1.1))
+    u = random_vector(d.mesh.ndof, 5, 0.01)
+    x = random_vector(d.mesh.ndof, 6)
+    b1 = 37.0
+    U, X = d.gather(u), d.gather(x)
+    ref = d.ref
+    Y = ref.tangent_action(U, X, d.mu, d.lam) + b1 * ref.mass_action(X, d.rho)
+    lhs = np.einsum("ecm,ecm->e", X, Y)
+    A = material.tangent(ref.deformation(U), d.mu, d.lam)
+    GX = ref.grad(X)
+    dP = np.einsum("eqiJkL,eqkL->eqiJ", A, GX)
+    VX = ref.values(X)
+    rhs = (np.einsum("eqiJ,eqiJ,q->e", GX, dP, ref.w)
+           + b1 * d.rho * np.einsum("eqc,eqc,q->e", VX, VX, ref.w))
+    assert np.allclose(lhs, rhs, rtol=1e-12, atol=1e-12 * np.abs(lhs).max())
+    # summed over elements it is x . (K x) of the assembled operator
+    assert np.isclose(lhs.sum(), x @ (d.tangent_apply(u, x) + b1 * d.mass_apply(x)), rtol=1e-11)
