@@ -92,6 +92,7 @@ struct sdme_batch {
   double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr, *d64 = nullptr, *x64 = nullptr;
   float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr, *x32 = nullptr;
   double *un = nullptr, *ahat = nullptr, *mhat = nullptr, *y = nullptr, *psi = nullptr, *du = nullptr;
+  int* loc = nullptr;         // per-problem tangent offset tables (even orders), concatenated
   // pinned host mirrors
   PcgScalars* scal_h = nullptr;
   double* dnorm_h = nullptr;
@@ -128,7 +129,7 @@ namespace {
 void batch_free(sdme_batch* b) {
   void* dev[] = {b->info, b->cta_prob, b->active, b->err, b->scal, b->partial, b->dcount, b->dnorm,
                  b->st64, b->st32, b->r64, b->p64, b->q64, b->d64, b->x64, b->r32, b->p32, b->q32,
-                 b->d32, b->x32, b->un, b->ahat, b->mhat, b->y, b->psi, b->du};
+                 b->d32, b->x32, b->un, b->ahat, b->mhat, b->y, b->psi, b->du, b->loc};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {b->scal_h, b->dnorm_h, b->err_h, b->active_h};
@@ -535,6 +536,32 @@ sdme_status sdme_batch_create(sdme_batch** out, const sdme_problem* probs, int n
          cudaMemsetAsync(b->scal, 0, sizeof(PcgScalars) * np, b->stream) == cudaSuccess &&
          cudaMemsetAsync(b->dcount, 0, sizeof(unsigned int) * np, b->stream) == cudaSuccess &&
          cudaStreamSynchronize(b->stream) == cudaSuccess;
+  }
+  if (ok) {
+    // tangent gather / scatter offset tables of the even-order problems:
+    // entry (c, r, q, p) at c Nn + (r N1 + q) N0 + p from the element corner
+    std::vector<int> tab;
+    std::vector<int64_t> toff(np, -1);
+    for (size_t i = 0; i < np; ++i) {
+      const Prob& pr = b->probs[i];
+      const HostMesh& h = pr.hm;
+      if (pr.P % 2 != 0 || 3 * h.Nn > (int64_t)INT32_MAX) continue;
+      const int n = pr.P + 1;
+      toff[i] = (int64_t)tab.size();
+      for (int c = 0; c < 3; ++c)
+        for (int r = 0; r < n; ++r)
+          for (int q = 0; q < n; ++q)
+            for (int pp = 0; pp < n; ++pp)
+              tab.push_back((int)(c * h.Nn + ((int64_t)r * h.N[1] + q) * h.N[0] + pp));
+    }
+    if (!tab.empty()) {
+      ok = dalloc(&b->loc, tab.size()) == cudaSuccess &&
+           cudaMemcpy(b->loc, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+      for (Group& g : b->groups)
+        for (HostBatchLaunch& L : g.launches)
+          for (size_t k = 0; ok && k < L.pid.size(); ++k)
+            if (toff[L.pid[k]] >= 0) L.mesh[k].loc = b->loc + toff[L.pid[k]];
+    }
   }
   if (!ok) {
     cudaGetLastError();

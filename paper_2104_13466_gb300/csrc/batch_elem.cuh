@@ -26,6 +26,7 @@ struct BatchParams {
   int64_t st_off[kBatchLaunchMax];        // offset of its Gauss-point state (words)
   int64_t part_off[kBatchLaunchMax];      // offset of its per-element partials
   MeshParams<T> m[kBatchLaunchMax];
+  const int* loc[kBatchLaunchMax];        // per-problem offset tables (ElemParams::loc), or null
 };
 static_assert(sizeof(BatchParams<double, 8>) <= 32000, "batch parameter block exceeds the kernel parameter limit");
 
@@ -68,7 +69,8 @@ batch_tangent_kernel(const __grid_constant__ BatchParams<T, P> bp, const TV* __r
     __syncthreads();
     tangent_body<P, T, TV, true>(bp.tab, bp.pairs, bp.m[k], w - bp.estart[k], x + off, y + off, st + bp.st_off[k],
                                  partial ? partial + bp.part_off[k] : nullptr,
-                                 (unsigned)(bp.estart[k + 1] - bp.estart[k]), scal ? scal + bp.pid[k] : nullptr, sm);
+                                 (unsigned)(bp.estart[k + 1] - bp.estart[k]), scal ? scal + bp.pid[k] : nullptr, sm,
+                                 bp.loc[k]);
   }
 }
 
@@ -125,6 +127,7 @@ static void make_batch_params(const HostElemData& tabs, const HostBatchLaunch& L
     bp->dof_off[k] = L.dof_off[k];
     bp->st_off[k] = L.st_off[k];
     bp->part_off[k] = L.part_off[k];
+    bp->loc[k] = h.loc;
   }
   bp->estart[bp->nprob] = bp->total;
 }

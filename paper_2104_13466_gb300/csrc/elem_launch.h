@@ -38,6 +38,7 @@ struct HostMesh {
   int N[3] = {0, 0, 0};
   int64_t Nn = 0;
   unsigned clamp[6] = {0, 0, 0, 0, 0, 0};
+  const int* loc = nullptr;          // device offset table of the tangent gather / scatter (or null)
 };
 
 // One batched element launch: up to kBatchLaunchMax problems of one order.
