@@ -208,6 +208,19 @@ def cpu_oracle_matvec(w, basis, nsample, seed=0):
     return dofs_per_s, dt, os.cpu_count()
 
 
+def workload_config(args, w, ws):
+    """The `config` object of the default line, identical for both arms."""
+    ne, P = w["elems"], w["P"]
+    nelem = int(np.prod(ne))
+    n = 3 * int(np.prod([e * P + 1 for e in ne]))
+    wstate = 4 if args.precision == "mixed" else 8
+    return {"workload": "beam_p8: [0,8]x[0,1]^2 cantilever, 64x8x8 hexes, P=8, %d DOFs, basis %s, "
+                        "%s, Newton tol %g, dt %g" % (n, args.basis, args.precision, w["newton_tol"], w["dt"]),
+            "global_batch": 1, "parallelism": "replicas" if ws > 1 else "single",
+            "l2": "inputs larger than L2 (vectors 52 MB each, Gauss-point state %d MB)"
+                  % (10 * (P + 2) ** 3 * nelem * wstate // 2 ** 20)}
+
+
 def run_reference(args, w):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -225,7 +238,7 @@ def run_reference(args, w):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "beam_p8: 64x8x8 hexes, P=8, 6502275 DOFs, basis %s" % args.basis},
+            "config": workload_config(args, w, ws),
             "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -331,11 +344,7 @@ def run_gpu(args, w):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32-matvec/f64-residual" if prec == sd.MIXED_FP32 else "f64",
             "data": "synthetic",
-            "config": {"workload": "beam_p8: [0,8]x[0,1]^2 cantilever, 64x8x8 hexes, P=8, %d DOFs, basis %s, "
-                                   "%s, Newton tol %g, dt %g" % (n, args.basis, args.precision, w["newton_tol"], dt),
-                       "global_batch": 1, "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "inputs larger than L2 (vectors 52 MB each, Gauss-point state %d MB)"
-                             % (10 * (w["P"] + 2) ** 3 * ctx.nelem * wstate // 2 ** 20)},
+            "config": workload_config(args, w, ws),
             "newton_pcg_ms_per_step": ms / args.steps,
             "steps_detail": [{k: s[k] for k in ("newton_iters", "pcg_iters_total", "converged")} for s in stats],
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
