@@ -92,3 +92,41 @@ def test_quad_affine_patch():
     u = np.concatenate([(G[c, 0] * XX + G[c, 1] * YY).ravel() for c in range(2)])
     R = d.internal_force(u).reshape(2, m.N[1], m.N[0])
     assert np.abs(R[:, 1:-1, 1:-1]).max() < 1e-10 * np.abs(R).max()
+
+
+def _static_fab_2d(ne, P, kind="sdme_h"):
+    # the paper's static fabricated field u = (1.9 sin x - x, 0) (Sec. 5.1) in
+    # plane strain on the unit square: body force, the exact P N on the loaded
+    # edges, x = 0 clamped
+    from oracle import manufactured, solvers
+    fld = manufactured.static_field()
+    m = quad.RectMesh(ne, ne, P).clamp("xmin")
+    d = quad.Discretization2D(m, Basis1D(P, kind), MU, LAM)
+    f = d.body_load(fld.body_force(MU, LAM, 1.0))
+    for e in ("xmax", "ymin", "ymax"):
+        f = f + d.traction_field_load(e, fld.traction(e, MU, LAM))
+    u, st = solvers.static_newton(d, f, tol=1e-12, linear="direct")
+    assert st["converged"] and st["newton_iters"] <= 6
+    return d.l2_error(u, fld.displacement)
+
+
+def test_edge_traction_field_reduces_to_uniform_and_body_load_to_area():
+    m = quad.RectMesh(2, 3, 3, (1.3, 0.7))
+    d = quad.Discretization2D(m, Basis1D(3, "nodal"), 1.0, 1.0)
+    t = np.array([0.3, -1.1])
+    for e in quad.EDGES:
+        assert np.allclose(d.traction_field_load(e, lambda X, tt: np.broadcast_to(t, X.shape)),
+                           d.traction_load(e, t), atol=1e-15)
+    f = d.body_load(lambda X, tt: np.broadcast_to(t, X.shape))
+    # nodal basis: partition of unity, so each component sums to b_c x area
+    assert np.allclose([f[:m.Nn].sum(), f[m.Nn:].sum()], t * 1.3 * 0.7, rtol=1e-13)
+
+
+def test_static_fabricated_field_converges_in_p_and_h():
+    errs = [_static_fab_2d(2, P) for P in range(1, 6)]
+    for a, b in zip(errs, errs[1:]):
+        assert np.all(b < a / 10.0)          # spectral in P on a fixed 2 x 2 mesh
+    assert errs[-1][0] < 1e-7
+    eh = [_static_fab_2d(ne, 2) for ne in (1, 2, 4)]
+    rates = [np.log2(a[0] / b[0]) for a, b in zip(eh, eh[1:])]
+    assert 2.8 < rates[-1] < 3.3                # L2 rate P + 1 at P = 2
