@@ -244,6 +244,130 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def make_context(sd, w, basis, prec, lam_h=None):
+    mu, lam = lame(w["E"], w["nu"])
+    return sd.Context(w["elems"], w["lengths"], w["clamp"], mu, lam, w["rho"], w["P"], basis, precision=prec,
+                      k=w["k"], lam_h=w["lam"] if lam_h is None else lam_h)
+
+
+class Ramp:
+    """Implicit Newmark steps of a workload's load ramp on one context, from
+    rest: step k applies the traction at level min(k, steps) / steps.  Each
+    step is timed with CUDA events on the current stream (the context runs on
+    the legacy default stream, which orders with it)."""
+
+    def __init__(self, sd, torch, ctx, w, opts):
+        self.sd, self.torch, self.ctx, self.w, self.opts = sd, torch, ctx, w, opts
+        n = ctx.ndof
+        self.unit = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ctx.traction_load(w["traction_face"], np.array(w["traction_dir"], dtype=float), self.unit)
+        self.smag = load_magnitude(w["load_key"])
+        self.u, self.v, self.a, self.Pn = (torch.zeros(n, dtype=torch.float64, device="cuda") for _ in range(4))
+        self.k = 0
+
+    def state(self):
+        return self.k, self.u.clone(), self.v.clone(), self.a.clone()
+
+    def set_state(self, st):
+        self.k = st[0]
+        for dst, src in zip((self.u, self.v, self.a), st[1:]):
+            dst.copy_(src)
+
+    def step(self):
+        torch = self.torch
+        self.k += 1
+        level = min(self.k, self.w["steps"])
+        torch.mul(self.unit, self.smag * level / self.w["steps"], out=self.Pn)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = self.ctx.implicit_newmark_step(self.u, self.v, self.a, self.w["dt"], self.Pn,
+                                            allow=(self.sd.NEWTON_DIVERGED,), **self.opts)
+        e1.record(stream)
+        e1.synchronize()
+        st["ms"] = e0.elapsed_time(e1)
+        st["level"] = level
+        return st
+
+
+def step_summary(st):
+    return {"level": st["level"], "ms": round(st["ms"], 3), "converged": st["converged"],
+            "newton_iters": st["newton_iters"], "pcg_iters_total": st["pcg_iters_total"],
+            "residual_rel": st["residual_rel"], "lin_rel_max": st["lin_rel_max"],
+            "refine_sweeps": st["refine_sweeps"]}
+
+
+def arm_summary(n, steps):
+    ms = sum(s["ms"] for s in steps)
+    mv = sum(s["matvecs"] for s in steps)
+    return {"steps": len(steps), "levels": [s["level"] for s in steps],
+            "converged_steps": sum(1 for s in steps if s["converged"]),
+            "ms_per_step": ms / max(1, len(steps)), "matvec_dofs_per_s": n * mv / (ms * 1e-3) if ms > 0 else None,
+            "newton_iters_per_step": sum(s["newton_iters"] for s in steps) / max(1, len(steps)),
+            "pcg_iters_per_newton": mv / max(1, sum(s["newton_iters"] for s in steps)),
+            "ms": [round(s["ms"], 2) for s in steps]}
+
+
+def newton_opts(args, w):
+    return dict(newton_tol=w["newton_tol"], pcg_rtol=w["pcg_rtol"], mixed_rtol=args.mixed_rtol,
+                pcg_maxit=args.pcg_maxit, max_newton=args.max_newton, forcing=args.forcing)
+
+
+def compare_block(args, w, n_main, main_steps, saved, prec_main):
+    """The metric's comparisons beside the timed line (rank 0):
+    * fp64 vs mixed on the cantilever: one float64 step from the main arm's
+      own input state at each saved level, against the main arm's step there;
+    * bases on the cantilever: each other basis from rest over the first
+      levels of the ramp, against the main arm's steps at the same levels;
+    * the unit cube of 4^3 hexes at P = 4 (14,739 DOFs, bottom clamped, top
+      traction ramped over 10 steps of dt = 0.01): every basis in both
+      precisions over the whole ramp."""
+    import torch
+    import paper_2104_13466_gb300 as sd
+    out = {}
+    opts = newton_opts(args, w)
+    other = sd.FP64 if prec_main == sd.MIXED_FP32 else sd.MIXED_FP32
+    ctx = make_context(sd, w, args.basis, other)
+    ramp = Ramp(sd, torch, ctx, w, opts)
+    rows = []
+    for lvl_state in saved:
+        ramp.set_state(lvl_state)
+        st = ramp.step()
+        mine = main_steps[lvl_state[0]]
+        rows.append({"level": st["level"], "mixed_ms" if prec_main == sd.MIXED_FP32 else "fp64_ms": mine["ms"],
+                     "fp64_ms" if prec_main == sd.MIXED_FP32 else "mixed_ms": st["ms"],
+                     "mixed_converged": mine["converged"] if prec_main == sd.MIXED_FP32 else st["converged"],
+                     "fp64_converged": st["converged"] if prec_main == sd.MIXED_FP32 else mine["converged"],
+                     "fp64_newton_iters": (st if prec_main == sd.MIXED_FP32 else mine)["newton_iters"],
+                     "mixed_newton_iters": (mine if prec_main == sd.MIXED_FP32 else st)["newton_iters"]})
+    ctx.close()
+    for r in rows:
+        r["mixed_speedup"] = r["fp64_ms"] / r["mixed_ms"]
+    out["beam_fp64_vs_mixed"] = rows
+    m = min(args.compare_levels, len(main_steps))
+    bases = {args.basis: arm_summary(n_main, main_steps[:m])}
+    for basis in [b for b in args.compare_bases.split(",") if b and b != args.basis]:
+        ctx = make_context(sd, w, basis, prec_main)
+        n = ctx.ndof
+        ramp = Ramp(sd, torch, ctx, w, opts)
+        bases[basis] = arm_summary(n, [ramp.step() for _ in range(m)])
+        ctx.close()
+    out["beam_bases"] = {"precision": "mixed" if prec_main == sd.MIXED_FP32 else "fp64", "arms": bases}
+    wc = workload("cube_p4")
+    cube = {}
+    for pname, pr in (("mixed", sd.MIXED_FP32), ("fp64", sd.FP64)):
+        for basis in ("nodal", "modal", "sdme_m", "sdme_h"):
+            ctx = make_context(sd, wc, basis, pr)
+            o = newton_opts(args, wc)
+            warm = Ramp(sd, torch, ctx, wc, o)
+            warm.step()
+            ramp = Ramp(sd, torch, ctx, wc, o)
+            cube["%s/%s" % (basis, pname)] = arm_summary(ctx.ndof, [ramp.step() for _ in range(wc["steps"])])
+            ctx.close()
+    out["cube_p4"] = cube
+    return out
+
+
 def run_gpu(args, w):
     import torch
     import paper_2104_13466_gb300 as sd
@@ -254,29 +378,24 @@ def run_gpu(args, w):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     prec = sd.MIXED_FP32 if args.precision == "mixed" else sd.FP64
-    mu, lam = lame(w["E"], w["nu"])
-    ctx = sd.Context(w["elems"], w["lengths"], w["clamp"], mu, lam, w["rho"], w["P"], args.basis, precision=prec)
+    ctx = make_context(sd, w, args.basis, prec)
     n = ctx.ndof
     dev = torch.device("cuda", local)
-    unit = torch.zeros(n, dtype=torch.float64, device=dev)
-    t = np.array(w["traction_dir"]) * 1.0
-    ctx.traction_load(w["traction_face"], t, unit)
-    smag = load_magnitude(w["load_key"])
-    u = torch.zeros(n, dtype=torch.float64, device=dev)
-    v = torch.zeros_like(u)
-    a = torch.zeros_like(u)
-    Pn = torch.zeros_like(u)
-    opts = dict(newton_tol=w["newton_tol"], pcg_rtol=w["pcg_rtol"], mixed_rtol=args.mixed_rtol,
-                pcg_maxit=args.pcg_maxit, max_newton=args.max_newton, forcing=args.forcing)
-    nsteps = w["steps"]
-    dt = w["dt"]
-    step_i = [0]
+    opts = newton_opts(args, w)
+    ramp = Ramp(sd, torch, ctx, w, opts)
+    # input states of the fp64-vs-mixed comparison: the first timed step and
+    # the last ramp level reached
+    total = args.warmup + args.steps
+    cmp_levels = sorted({args.warmup + 1, min(total, w["steps"])})
+    saved = []
+    all_steps = []
 
     def one_step():
-        step_i[0] += 1
-        k = min(step_i[0], nsteps)
-        torch.mul(unit, smag * k / nsteps, out=Pn)
-        return ctx.implicit_newmark_step(u, v, a, dt, Pn, allow=(sd.NEWTON_DIVERGED, sd.PCG_MAXIT), **opts)
+        if ramp.k + 1 in cmp_levels and rank == 0 and not args.no_compare:
+            saved.append(ramp.state())
+        st = ramp.step()
+        all_steps.append(st)
+        return st
 
     for _ in range(args.warmup):
         one_step()
@@ -299,7 +418,8 @@ def run_gpu(args, w):
     t1 = ctx.timing()
     ms = max_over_ranks(e0.elapsed_time(e1), dev)
     matvecs = sum(s["matvecs"] for s in stats)
-    value = replica_throughput(ws, n, matvecs, ms)
+    unconverged = sum(1 for s in all_steps if not s["converged"])
+    value = replica_throughput(ws, n, matvecs, ms) if unconverged == 0 else None
     tan_ms = (t1["tangent_ms"] - t0["tangent_ms"])
     tan_launches = t1["tangent_launches"] - t0["tangent_launches"]
     avg_tan = tan_ms / max(1, tan_launches)
@@ -311,33 +431,41 @@ def run_gpu(args, w):
     hbm_peak, hbm_src = _peaks()
     achieved_gbs = nbytes / (avg_tan * 1e-3) / 1e9
 
-    # end to end through the public API: host state and load in, host state out
+    # end to end through the public API: host state and load in, host state
+    # out, for the step after the timed ones (same load level as the last)
     pin = [torch.zeros(n, dtype=torch.float64).pin_memory() for _ in range(4)]
-    for p_, d_ in zip(pin, (u, v, a, unit)):
+    for p_, d_ in zip(pin, (ramp.u, ramp.v, ramp.a, ramp.unit)):
         p_.copy_(d_)
     out = [torch.zeros(n, dtype=torch.float64).pin_memory() for _ in range(3)]
     torch.cuda.synchronize()
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_mv = 0
+    e2e_mv, e2e_conv = 0, True
     e2.record(stream)
     for _ in range(args.e2e_steps):
-        for p_, d_ in zip(pin, (u, v, a, unit)):
+        for p_, d_ in zip(pin, (ramp.u, ramp.v, ramp.a, ramp.unit)):
             d_.copy_(p_, non_blocking=True)
-        e2e_mv += one_step()["matvecs"]
-        for o_, d_ in zip(out, (u, v, a)):
+        ramp.k -= 1  # the same load level as the last timed step
+        st = ramp.step()
+        e2e_mv += st["matvecs"]
+        e2e_conv = e2e_conv and st["converged"]
+        for o_, d_ in zip(out, (ramp.u, ramp.v, ramp.a)):
             o_.copy_(d_, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e2.elapsed_time(e3)
-    e2e_value = ws * n * e2e_mv / (e2e_ms * 1e-3) if e2e_ms > 0 else None
+    e2e_value = ws * n * e2e_mv / (e2e_ms * 1e-3) if e2e_ms > 0 and e2e_conv else None
+    ctx.close()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cv, cdt, cores = cpu_oracle_matvec(w, args.basis, args.ref_sample)
         cpu = {"value": cv, "unit": "DOF/s", "cores": cores, "kind": "oracle",
                "sample": "FP64 numpy oracle tangent action on %d of %d elements (%.1f s), scaled to the mesh"
-                         % (args.ref_sample, ctx.nelem, cdt)}
+                         % (args.ref_sample, int(np.prod(w["elems"])), cdt)}
     clocks = clk.summary()
+    compare = None
+    if rank == 0 and not args.no_compare:
+        compare = compare_block(args, w, n, all_steps, saved, prec)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
@@ -346,7 +474,8 @@ def run_gpu(args, w):
             "data": "synthetic",
             "config": workload_config(args, w, ws),
             "newton_pcg_ms_per_step": ms / args.steps,
-            "steps_detail": [{k: s[k] for k in ("newton_iters", "pcg_iters_total", "converged")} for s in stats],
+            "unconverged_steps": unconverged,
+            "steps_detail": [step_summary(s) for s in all_steps[args.warmup:]],
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved_tf / alu_peak,
                          "traffic": profiled_traffic(args.precision) if w["P"] == 8 and args.workload == "beam_p8"
@@ -362,10 +491,13 @@ def run_gpu(args, w):
             "gpu_launches": int(t1["kernel_launches"] - t0["kernel_launches"]),
             "clocks": clocks,
         }
+        if compare is not None:
+            line["compare"] = compare
         print(json.dumps(line), flush=True)
-    ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+    if unconverged:
+        sys.exit(1)
 
 
 def run_kernel_only(args, w):
@@ -721,6 +853,10 @@ def main():
     ap.add_argument("--energy-every", type=int, default=50)
     ap.add_argument("--dt-iters", type=int, default=100)
     ap.add_argument("--bases", default="nodal,modal,sdme_m,sdme_h")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the basis / precision / unit-cube comparisons printed beside the default line")
+    ap.add_argument("--compare-bases", default="nodal,modal,sdme_m,sdme_k")
+    ap.add_argument("--compare-levels", type=int, default=5)
     ap.add_argument("--precisions", default="mixed,fp64")
     ap.add_argument("--kernel-iters", type=int, default=20)
     ap.add_argument("--adjoint", action="store_true")

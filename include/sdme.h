@@ -67,8 +67,12 @@ typedef enum {
 typedef enum {
   SDME_FP64 = 0,      /* everything in float64 */
   SDME_MIXED_FP32 = 1 /* tangent matvec, diagonal and PCG vectors in float32;
-                         Newton residual, dot-product reductions, PCG scalars
-                         and time-integrator state in float64 */
+                         Newton residual, PCG scalars and time-integrator state
+                         in float64.  PCG dot products: float32 products (of
+                         float32 vectors, summed four at a time) accumulated
+                         per thread and reduced in float64; the operator's
+                         p.(A p) from float32 Gauss-point terms accumulated in
+                         float64 */
 } sdme_precision;
 
 enum { SDME_XMIN = 0, SDME_XMAX = 1, SDME_YMIN = 2, SDME_YMAX = 3, SDME_ZMIN = 4, SDME_ZMAX = 5 };
@@ -106,7 +110,9 @@ typedef struct {
 
 typedef struct {
   double beta, gamma;    /* Newmark parameters (reading of the garbled table: 0.25, 0.5) */
-  double newton_tol;     /* stop when ||psi_k|| <= tol * max(||psi_0||, 1e-14 ||P||) */
+  double newton_tol;     /* stop when ||psi_k|| <= tol * max(||psi_0||, ||P||): the
+                            paper's tolerance (Sec. 5.1) relative to the larger of
+                            the step's initial residual and the applied load */
   int max_newton;
   double pcg_rtol;       /* FP64: ||r|| <= rtol ||b|| */
   double mixed_rtol;     /* MIXED_FP32: inner PCG tolerance (inexact Newton) */
@@ -128,6 +134,10 @@ typedef struct {
   double residual_final;       /* ||psi|| at exit */
   int pcg_iters[32];           /* per Newton iteration (first 32) */
   double residuals[33];        /* ||psi_k||, k = 0..min(newton_iters, 32) */
+  double residual_ref;         /* max(||psi_0||, ||P||): the Newton test's reference */
+  int refine_sweeps;           /* MIXED_FP32: float64 refinement restarts of the PCG solves */
+  double lin_rel_max;          /* MIXED_FP32: largest float64 relative residual
+                                  ||psi - (b1 M + K_T) du|| / ||psi|| of the step's solves */
 } sdme_step_stats;
 
 typedef struct {
@@ -227,6 +237,13 @@ sdme_status sdme_diagonal(sdme_ctx* ctx, const double* u_dev, double b1, double*
  * stopping when ||r||_2 <= rtol ||b||_2 (CGD of Sec. 5).  Writes the
  * iteration count and the final relative residual (host pointers, may be
  * NULL).  SDME_PCG_MAXIT when maxit is reached.
+ * SDME_MIXED_FP32: the iterations run in float32 with the solution summed in
+ * float64; when the float32 recurrence meets the test, the float64 residual
+ * b - (b1 M + K_T(u)) x is formed with the float64 operator (the stored
+ * float64 state) and the recurrence restarts from it until that residual
+ * meets the test (iterative refinement; at most the restarts set by
+ * sdme_set_refinement, each required to halve the residual).  final_rel is
+ * then the float64 residual's.
  */
 sdme_status sdme_pcg_solve(sdme_ctx* ctx, const double* u_dev, double b1, const double* b_dev,
                            double* x_dev, double rtol, int maxit, int* iters, double* final_rel);
@@ -262,7 +279,7 @@ sdme_status sdme_set_condensation(sdme_ctx* ctx, int enable);
  * pcg_rtol in FP64, mixed_rtol in MIXED_FP32), u += du, until
  * ||psi|| <= newton_tol max(||psi_0||, 1e-14 ||P||) or max_newton
  * iterations.  u_dev: initial guess in, solution out (constrained entries
- * are kept).  opts may be NULL (tol 1e-8, 50 iterations, pcg_rtol 1e-12);
+ * are kept; the last iterate when the test is not met).  opts may be NULL (tol 1e-8, 50 iterations, pcg_rtol 1e-12);
  * beta and gamma are ignored.  Returns SDME_OK when converged,
  * SDME_NEWTON_DIVERGED otherwise, or the inner solver's failure.
  * Synchronises.
@@ -279,6 +296,10 @@ sdme_status sdme_static_solve(sdme_ctx* ctx, double* u_dev, const double* P_dev,
  * P_next_dev: external load at t_{n+1} (device, ndof).  Constrained entries of
  * state->u keep their values.  opts NULL selects defaults
  * (0.25, 0.5, 1e-8, 30, 1e-10, 1e-4, 20000).  stats may be NULL.
+ * Returns SDME_OK when the Newton test is met.  Otherwise (SDME_NEWTON_DIVERGED
+ * after max_newton iterations, SDME_NONPOSITIVE_J, SDME_NAN or the inner
+ * solver's failure) the state is left at t_n: u is restored to u_n and v, a
+ * are not touched; stats describe the failed attempt.
  */
 sdme_status sdme_implicit_newmark_step(sdme_ctx* ctx, sdme_state* state, double dt,
                                        const double* P_next_dev, const sdme_newton_opts* opts,
@@ -403,6 +424,15 @@ const char* sdme_cuda_error_string(const sdme_ctx* ctx);
 
 /* Enable (1) / disable (0) CUDA-event timing of every tangent-kernel launch. */
 sdme_status sdme_set_timing(sdme_ctx* ctx, int enable);
+
+/*
+ * MIXED_FP32 contexts: the largest number of float64-residual restarts
+ * (iterative refinement) of one float32 PCG solve; 0 turns the refinement
+ * off (the float32 recurrence's own test ends the solve).  Default 8.
+ * Applies to the tangent and mass solves; ignored by FP64 contexts.
+ * SDME_EINVAL for a negative count.
+ */
+sdme_status sdme_set_refinement(sdme_ctx* ctx, int max_restarts);
 sdme_status sdme_get_timing(sdme_ctx* ctx, sdme_timing* out);
 
 /*

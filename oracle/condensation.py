@@ -67,7 +67,7 @@ def static_newton_condensed(disc, Pext, tol=1e-8, cg_rtol=1e-12, maxnewton=50):
         psi[disc.mask] = 0.0
         nrm = np.linalg.norm(psi)
         psi0 = nrm if psi0 is None else psi0
-        if nrm <= tol * max(psi0, 1e-14 * np.linalg.norm(Pext)):
+        if nrm <= tol * max(psi0, np.linalg.norm(Pext)):
             return u, {"converged": True, "newton_iters": k, "cg_iters": its}
         if k == maxnewton:
             break

@@ -37,7 +37,7 @@ EXPORTS = ("sdme_status_string", "sdme_build_basis1d", "sdme_create", "sdme_dest
            "sdme_explicit_forward", "sdme_explicit_adjoint", "sdme_batch_create", "sdme_batch_destroy",
            "sdme_batch_layout", "sdme_batch_internal_force", "sdme_batch_tangent_apply", "sdme_batch_traction_load",
            "sdme_batch_newmark_step", "sdme_batch_tune", "sdme_batch_launches", "sdme_static_solve",
-           "sdme_set_condensation")
+           "sdme_set_condensation", "sdme_set_refinement")
 
 
 class BasisDesc(ctypes.Structure):
@@ -66,7 +66,8 @@ class NewtonOpts(ctypes.Structure):
 class StepStats(ctypes.Structure):
     _fields_ = [("newton_iters", ctypes.c_int), ("pcg_iters_total", ctypes.c_int), ("matvecs", ctypes.c_int),
                 ("converged", ctypes.c_int), ("residual0", ctypes.c_double), ("residual_final", ctypes.c_double),
-                ("pcg_iters", ctypes.c_int * 32), ("residuals", ctypes.c_double * 33)]
+                ("pcg_iters", ctypes.c_int * 32), ("residuals", ctypes.c_double * 33),
+                ("residual_ref", ctypes.c_double), ("refine_sweeps", ctypes.c_int), ("lin_rel_max", ctypes.c_double)]
 
 
 class State(ctypes.Structure):
@@ -137,6 +138,7 @@ def _load():
     lib.sdme_static_solve.argtypes = [vp, vp, vp, ctypes.POINTER(NewtonOpts), ctypes.POINTER(StepStats)]
     lib.sdme_set_condensation.argtypes = [vp, i]
     lib.sdme_set_timing.argtypes = [vp, i]
+    lib.sdme_set_refinement.argtypes = [vp, i]
     lib.sdme_get_timing.argtypes = [vp, ctypes.POINTER(Timing)]
     lib.sdme_tangent_apply_noalloc.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(Material), i, pd, pd, pd,
                                                pd, vp, d, vp, vp, vp]
@@ -228,10 +230,13 @@ def tangent_apply_noalloc(elems, lengths, clamp, mu, lam, rho, P, tables, u, b1,
 
 def _stats_dict(stats, status):
     n = min(stats.newton_iters, 32)
+    ref = stats.residual_ref
     return {"status": status, "newton_iters": stats.newton_iters, "pcg_iters_total": stats.pcg_iters_total,
             "matvecs": stats.matvecs, "converged": bool(stats.converged), "residual0": stats.residual0,
-            "residual_final": stats.residual_final, "pcg_iters": list(stats.pcg_iters[:n]),
-            "residuals": list(stats.residuals[:n + 1])}
+            "residual_final": stats.residual_final, "residual_ref": ref,
+            "residual_rel": stats.residual_final / ref if ref > 0 else 0.0,
+            "refine_sweeps": stats.refine_sweeps, "lin_rel_max": stats.lin_rel_max,
+            "pcg_iters": list(stats.pcg_iters[:n]), "residuals": list(stats.residuals[:n + 1])}
 
 
 class _ExplicitStateHolder:
@@ -421,6 +426,10 @@ class Context:
 
     def set_timing(self, enable=True):
         return _check(lib.sdme_set_timing(self._h, int(bool(enable))), "sdme_set_timing")
+
+    def set_refinement(self, max_restarts):
+        """Float64-residual restarts allowed per float32 PCG solve (0: off)."""
+        return _check(lib.sdme_set_refinement(self._h, int(max_restarts)), "sdme_set_refinement")
 
     def timing(self):
         t = Timing()

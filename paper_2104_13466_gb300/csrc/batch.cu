@@ -707,11 +707,14 @@ sdme_status sdme_batch_newmark_step(sdme_batch* b, sdme_state* state, double dt,
         b->active_h[i] = 0;
         continue;
       }
-      if (psi0[i] < 0.0) psi0[i] = nrm;
+      if (psi0[i] < 0.0) {
+        psi0[i] = nrm;
+        st[i].residual_ref = std::max(nrm, pnorm[i]);
+      }
       if (k < 33) st[i].residuals[k] = nrm;
       st[i].residual_final = nrm;
       st[i].newton_iters = k;
-      if (nrm <= o.newton_tol * std::max(psi0[i], 1e-14 * pnorm[i])) {
+      if (nrm <= o.newton_tol * st[i].residual_ref) {
         res[i] = SDME_OK;
         st[i].converged = 1;
         b->active_h[i] = 0;

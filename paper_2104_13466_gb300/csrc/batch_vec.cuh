@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kVecThreads) kb_pcg_init(const BatchVecInfo* _
                                                            const int* __restrict__ active, double rtol, int maxit) {
   const BatchCta b(info, cta_prob);
   const bool act = active[b.p] != 0;
-  TV srz = TV(0), srr = TV(0);
+  double srz = 0.0, srr = 0.0;
   for (int64_t g = b.t0; g < b.mi.ndof; g += b.stride) {
     const int64_t i = b.off + g;
     const TV rv = (!act || dof_constrained(b.mi, g)) ? TV(0) : (TV)rhs[i];
@@ -131,10 +131,10 @@ __global__ void __launch_bounds__(kVecThreads) kb_pcg_init(const BatchVecInfo* _
     p[i] = z;
     x[i] = TV(0);
     q[i] = TV(0);
-    srz += rv * z;
-    srr += rv * rv;
+    srz += (double)(rv * z);
+    srr += (double)(rv * rv);
   }
-  double a = (double)srz, c = (double)srr;
+  double a = srz, c = srr;
   block_sum2(a, c);
   if (threadIdx.x == 0) {
     partial[2 * blockIdx.x] = a;
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kVecThreads) kb_pcg_update(const BatchVecInfo*
   using V = typename Vec16<TV>::type;
   constexpr int W = Vec16<TV>::width;
   const TV alpha = (TV)sc->alpha;
-  TV srz = TV(0), srr = TV(0);
+  double srz = 0.0, srr = 0.0;
   TV *xs = x + b.off, *rs = r + b.off, *qs = q + b.off;
   const TV *ps = p + b.off, *ds = dinv + b.off;
   const int64_t n = b.mi.ndof, nv = n / W;
@@ -187,14 +187,17 @@ __global__ void __launch_bounds__(kVecThreads) kb_pcg_update(const BatchVecInfo*
     V pv = reinterpret_cast<const V*>(ps)[g];
     V qv = reinterpret_cast<const V*>(qs)[g];
     V dv = reinterpret_cast<const V*>(ds)[g];
+    TV vrz = TV(0), vrr = TV(0);
 #pragma unroll
     for (int i = 0; i < W; ++i) {
       lane(xv, i) += alpha * lane(pv, i);
       const TV ri = lane(rv, i) - alpha * lane(qv, i);
       lane(rv, i) = ri;
-      srz += ri * (lane(dv, i) * ri);
-      srr += ri * ri;
+      vrz += ri * (lane(dv, i) * ri);
+      vrr += ri * ri;
     }
+    srz += (double)vrz;
+    srr += (double)vrr;
     reinterpret_cast<V*>(xs)[g] = xv;
     reinterpret_cast<V*>(rs)[g] = rv;
     reinterpret_cast<V*>(qs)[g] = V{};
@@ -205,10 +208,10 @@ __global__ void __launch_bounds__(kVecThreads) kb_pcg_update(const BatchVecInfo*
     const TV rv = rs[g] - alpha * qv;
     rs[g] = rv;
     qs[g] = TV(0);
-    srz += rv * (ds[g] * rv);
-    srr += rv * rv;
+    srz += (double)(rv * (ds[g] * rv));
+    srr += (double)(rv * rv);
   }
-  double a = (double)srz, c = (double)srr;
+  double a = srz, c = srr;
   block_sum2(a, c);
   if (threadIdx.x == 0) {
     partial[2 * blockIdx.x] = a;

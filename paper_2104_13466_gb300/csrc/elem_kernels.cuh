@@ -669,16 +669,17 @@ constexpr int tangent_min_blocks() {
 // shared layout): forward stages, pointwise linearised stress (and the fused
 // mass term), transposed stages; the result replaces X.
 template <int P, typename T, bool STIFF>
-__device__ __forceinline__ T tangent_core(const ElemTables<T, P>& tb, int pairs, const MeshParams<T>& m, int e,
-                                          const T* __restrict__ st, T* sm) {
+__device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int pairs, const MeshParams<T>& m,
+                                               int e, const T* __restrict__ st, T* sm) {
   using G = Geo<P>;
   // float32: returns this thread's share of x_e . (K_e x_e).  The
   // transposed stages are the exact adjoint of the forward ones, so the
   // element product equals the quadrature form
-  // sum_q w_q (dF : dP + b1 rho |x(q)|^2), summed here at no memory cost.
+  // sum_q w_q (dF : dP + b1 rho |x(q)|^2), summed here at no memory cost
+  // (each Gauss point's term in float32, accumulated in float64).
   // float64 (bound by the float64 pipe) returns 0; its caller re-reads x.
   constexpr bool QDOT = sizeof(T) == 4;
-  T dotq = T(0);
+  double dotq = 0.0;
   constexpr int Q = P + 2, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
   constexpr int NT = G::NT;
   forward_stages<T, P, STIFF>(tb, pairs, sm);
@@ -693,7 +694,7 @@ __device__ __forceinline__ T tangent_core(const ElemTables<T, P>& tb, int pairs,
       for (int c = 0; c < 3; ++c) {
         const T u = sm[c * FQ + so];
         sm[c * FQ + so] = u * mfac;
-        if (QDOT) dotq += mfac * u * u;
+        if (QDOT) dotq += (double)(mfac * u * u);
       }
     }
   }
@@ -740,7 +741,7 @@ __device__ __forceinline__ T tangent_core(const ElemTables<T, P>& tb, int pairs,
       sm[c * FQ + so] = u * mfac;
       if (QDOT) mq += u * u;
     }
-    if (QDOT) dotq += wdet * qf + mfac * mq;
+    if (QDOT) dotq += (double)(wdet * qf + mfac * mq);
   }
   __syncthreads();
   transpose_stages<T, P, STIFF>(tb, pairs, sm);
@@ -790,7 +791,7 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
   }
   __syncthreads();
   if (stat0 != 0) return;
-  T dotT = tangent_core<P, T, STIFF>(tb, pairs, m, e, st, sm);
+  double dotT = tangent_core<P, T, STIFF>(tb, pairs, m, e, st, sm);
   constexpr bool RELOAD = sizeof(T) == 8;  // float64: x_e . y_e from a second read of x
   if (fast) {
     const TV* xb = x + view.base;
@@ -800,7 +801,7 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
       const int o = __ldg(loc + idx);
       const T v = X[idx];
       atomicAdd(&yb[o], (TV)v);
-      if (RELOAD && dot_partial) dotT += v * (T)xb[o];
+      if (RELOAD && dot_partial) dotT += (double)(v * (T)xb[o]);
     }
   } else {
 #pragma unroll
@@ -811,16 +812,16 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
       if (!cons) {
         const T v = X[so];
         atomicAdd(&y[g], (TV)v);
-        if (RELOAD && dot_partial) dotT += v * (T)x[g];
+        if (RELOAD && dot_partial) dotT += (double)(v * (T)x[g]);
       }
     }
   }
   if (dot_partial) {
     // x_e . (K_e x_e) summed over elements gives x . (K x) for the PCG step
-    // length (x_e is zero on constrained entries); summed in T within the
-    // CTA, float64 across CTAs in a fixed order: by the last CTA to finish
-    // here, or (defer) by every CTA of the following PCG update.
-    const double tot = static_cast<double>(block_sum_t(dotT));
+    // length (x_e is zero on constrained entries); float64 within the CTA
+    // and across CTAs in a fixed order: by the last CTA to finish here, or
+    // (defer) by every CTA of the following PCG update.
+    const double tot = block_sum(dotT);
     if (threadIdx.x == 0) dot_partial[e] = tot;
     if (scal && !defer && last_arrival(&scal->counter, nparts)) {
       const double pq = ordered_sum(dot_partial, (int)nparts);

@@ -251,7 +251,7 @@ quad_tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __re
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int e = blockIdx.x * kQuadWarps + w;
   const MeshParams<T>& m = prm;
-  T dotT = T(0);
+  double dotT = 0.0;
   if (e < m.ne[0] * m.ne[1]) {
     T* sm = reinterpret_cast<T*>(smem_raw) + w * G::WORDS;
     T* RU = sm;
@@ -308,13 +308,13 @@ quad_tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __re
       if (!cons) {
         const T v = RX[so];
         atomicAdd(&y[g], (TV)v);
-        if (dot_partial) dotT += v * (T)x[g];
+        if (dot_partial) dotT += (double)(v * (T)x[g]);
       }
     }
   }
   if (dot_partial) {
     double pq = 0.0;
-    if (quad_cta_reduce((double)dotT, dot_partial, scal ? &scal->counter : nullptr, &pq) && scal &&
+    if (quad_cta_reduce(dotT, dot_partial, scal ? &scal->counter : nullptr, &pq) && scal &&
         threadIdx.x == 0) {
       scal->pq = pq;
       scal->alpha = scal->rz / pq;

@@ -109,34 +109,41 @@ __global__ void __launch_bounds__(kVecThreads) k_axpy(int64_t n, double alpha, c
 }
 
 //----------------------------------------------------------------------------
-// Jacobi PCG (CGD).  Vectors in TV; dinv = 1 / diag.
+// Jacobi PCG (CGD).  Vectors r, p, q, dinv in TV (dinv = 1 / diag); the
+// solution x in TX (float64 for both precisions: a float32 x would bound
+// the float64 residual b - A x at about eps32 |A| |x|).
 //   init:      r = scale*b (0 on constrained), x = 0, q = 0, p = z = dinv r,
 //              rz = r.z, bb = r.r
 //   per iteration:  tangent kernel: q = A p, pq = p.q, alpha = rz / pq
 //                   update:    x += alpha p, r -= alpha q, q = 0,
 //                              rz' = r.(dinv r), rr = r.r, test, beta = rz'/rz
 //                   direction: p = dinv r + beta p
-// Per-thread partial sums run in TV; reductions across threads in float64.
+//   restart:   r = a given float64 residual, p = z = dinv r (x, bb, tol2 and
+//              the iteration count kept): the refinement step of the float32
+//              solve.
+// Dot products: each product in TV (float32 products of float32 vectors are
+// summed four at a time, one 16-byte vector), accumulated per thread and
+// reduced across threads in float64.
 //----------------------------------------------------------------------------
-template <typename TV>
+template <typename TV, typename TX>
 __global__ void __launch_bounds__(kVecThreads) k_pcg_init(MeshInfo mi, const double* __restrict__ b, double scale,
-                                                          const TV* __restrict__ dinv, TV* __restrict__ x,
+                                                          const TV* __restrict__ dinv, TX* __restrict__ x,
                                                           TV* __restrict__ r, TV* __restrict__ p,
                                                           TV* __restrict__ q, PcgScalars* scal,
                                                           double* __restrict__ partial, double rtol, int maxit) {
-  TV srz = TV(0), srr = TV(0);
+  double srz = 0.0, srr = 0.0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
        g += (int64_t)gridDim.x * blockDim.x) {
     const TV rv = dof_constrained(mi, g) ? TV(0) : (TV)(scale * b[g]);
     const TV z = dinv[g] * rv;
     r[g] = rv;
     p[g] = z;
-    x[g] = TV(0);
+    x[g] = TX(0);
     q[g] = TV(0);
-    srz += rv * z;
-    srr += rv * rv;
+    srz += (double)(rv * z);
+    srr += (double)(rv * rv);
   }
-  double a = (double)srz, c = (double)srr;
+  double a = srz, c = srr;
   block_sum2(a, c);
   if (threadIdx.x == 0) {
     partial[2 * blockIdx.x] = a;
@@ -185,8 +192,14 @@ __device__ __forceinline__ auto& lane(V& v, int i) {
   return reinterpret_cast<typename std::remove_reference<decltype(v.x)>::type*>(&v)[i];
 }
 
-template <typename TV>
-__global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TV* __restrict__ x, TV* __restrict__ r,
+// W consecutive entries of the solution vector (16 or 32 bytes).
+template <typename TX, int W>
+struct alignas(sizeof(TX) * W) XPack {
+  TX v[W];
+};
+
+template <typename TV, typename TX>
+__global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TX* __restrict__ x, TV* __restrict__ r,
                                                             const TV* __restrict__ p, TV* __restrict__ q,
                                                             const TV* __restrict__ dinv, PcgScalars* scal,
                                                             double* __restrict__ partial,
@@ -195,15 +208,17 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TV* __res
   if (scal->status != kPcgRunning) return;
   using V = typename Vec16<TV>::type;
   constexpr int W = Vec16<TV>::width;
+  using XP = XPack<TX, W>;
   const int64_t nv = n / W;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   // the first chunk's loads do not depend on the step length: issue them
   // before it is summed so that their latency overlaps the sum
-  V x0, r0, p0, q0, d0;
+  XP x0;
+  V r0, p0, q0, d0;
   const bool first = t0 < nv;
   if (first) {
-    x0 = reinterpret_cast<const V*>(x)[t0];
+    x0 = reinterpret_cast<const XP*>(x)[t0];
     r0 = reinterpret_cast<const V*>(r)[t0];
     p0 = reinterpret_cast<const V*>(p)[t0];
     q0 = reinterpret_cast<const V*>(q)[t0];
@@ -227,17 +242,21 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TV* __res
     alpha_d = scal->alpha;
   }
   const TV alpha = (TV)alpha_d;
-  TV srz = TV(0), srr = TV(0);
-  auto body = [&](V& xv, V& rv, V& pv, V& qv, V& dv, int64_t g) {
+  const TX alpha_x = (TX)alpha_d;
+  double srz = 0.0, srr = 0.0;
+  auto body = [&](XP& xv, V& rv, V& pv, V& qv, V& dv, int64_t g) {
+    TV vrz = TV(0), vrr = TV(0);
 #pragma unroll
     for (int i = 0; i < W; ++i) {
-      lane(xv, i) += alpha * lane(pv, i);
+      xv.v[i] += alpha_x * (TX)lane(pv, i);
       const TV ri = lane(rv, i) - alpha * lane(qv, i);
       lane(rv, i) = ri;
-      srz += ri * (lane(dv, i) * ri);
-      srr += ri * ri;
+      vrz += ri * (lane(dv, i) * ri);
+      vrr += ri * ri;
     }
-    reinterpret_cast<V*>(x)[g] = xv;
+    srz += (double)vrz;
+    srr += (double)vrr;
+    reinterpret_cast<XP*>(x)[g] = xv;
     reinterpret_cast<V*>(r)[g] = rv;
     reinterpret_cast<V*>(q)[g] = V{};
   };
@@ -249,10 +268,11 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TV* __res
   // two chunks per trip (ten 16-byte loads in flight per thread), same
   // chunk order as a one-chunk loop
   for (; g + stride < nv; g += 2 * stride) {
-    V xv[2], rv[2], pv[2], qv[2], dv[2];
+    XP xv[2];
+    V rv[2], pv[2], qv[2], dv[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      xv[u] = reinterpret_cast<const V*>(x)[g + u * stride];
+      xv[u] = reinterpret_cast<const XP*>(x)[g + u * stride];
       rv[u] = reinterpret_cast<const V*>(r)[g + u * stride];
       pv[u] = reinterpret_cast<const V*>(p)[g + u * stride];
       qv[u] = reinterpret_cast<const V*>(q)[g + u * stride];
@@ -262,7 +282,7 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TV* __res
     for (int u = 0; u < 2; ++u) body(xv[u], rv[u], pv[u], qv[u], dv[u], g + u * stride);
   }
   for (; g < nv; g += stride) {
-    V xv = reinterpret_cast<const V*>(x)[g];
+    XP xv = reinterpret_cast<const XP*>(x)[g];
     V rv = reinterpret_cast<const V*>(r)[g];
     V pv = reinterpret_cast<const V*>(p)[g];
     V qv = reinterpret_cast<const V*>(q)[g];
@@ -271,14 +291,14 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TV* __res
   }
   for (int64_t g = nv * W + t0; g < n; g += stride) {  // tail
     const TV qv = q[g];
-    x[g] += alpha * p[g];
+    x[g] += alpha_x * (TX)p[g];
     const TV rv = r[g] - alpha * qv;
     r[g] = rv;
     q[g] = TV(0);
-    srz += rv * (dinv[g] * rv);
-    srr += rv * rv;
+    srz += (double)(rv * (dinv[g] * rv));
+    srr += (double)(rv * rv);
   }
-  double a = (double)srz, c = (double)srr;
+  double a = srz, c = srr;
   block_sum2(a, c);
   if (threadIdx.x == 0) {
     partial[2 * blockIdx.x] = a;
@@ -324,6 +344,51 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_direction(int64_t n, const 
     reinterpret_cast<V*>(p)[g] = pv;
   }
   for (int64_t g = nv * W + t0; g < n; g += stride) p[g] = dinv[g] * r[g] + beta * p[g];
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(kVecThreads) k_pcg_restart(MeshInfo mi, const double* __restrict__ rt,
+                                                             const TV* __restrict__ dinv, TV* __restrict__ r,
+                                                             TV* __restrict__ p, TV* __restrict__ q, PcgScalars* scal,
+                                                             double* __restrict__ partial) {
+  double srz = 0.0, srr = 0.0;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const TV rv = dof_constrained(mi, g) ? TV(0) : (TV)rt[g];
+    const TV z = dinv[g] * rv;
+    r[g] = rv;
+    p[g] = z;
+    q[g] = TV(0);
+    srz += (double)(rv * z);
+    srr += (double)(rv * rv);
+  }
+  double a = srz, c = srr;
+  block_sum2(a, c);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = a;
+    partial[2 * blockIdx.x + 1] = c;
+  }
+  if (last_block_done(&scal->counter2)) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+      s0 += ((volatile double*)partial)[2 * i];
+      s1 += ((volatile double*)partial)[2 * i + 1];
+    }
+    block_sum2(s0, s1);
+    if (threadIdx.x == 0) {
+      scal->rz = s0;
+      scal->rr = s1;
+      scal->alpha = 0.0;
+      scal->beta = 0.0;
+      scal->pq = 0.0;
+      if (!isfinite(s0) || !isfinite(s1)) scal->status = kPcgBreakdown;
+      else if (s1 <= scal->tol2) scal->status = kPcgConverged;
+      else if (scal->iter >= scal->maxit) scal->status = kPcgMaxit;
+      else scal->status = kPcgRunning;
+      scal->counter = 0;
+      scal->counter2 = 0;
+    }
+  }
 }
 
 // out = scale * x (TV -> float64)

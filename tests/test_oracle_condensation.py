@@ -75,7 +75,7 @@ def _newmark_condensed_iterations(P, kind, dt, T):
             psi[d.mask] = 0.0
             nrm = np.linalg.norm(psi)
             psi0 = nrm if psi0 is None else psi0
-            if nrm <= 1e-12 * max(psi0, 1e-14 * np.linalg.norm(Pn)):
+            if nrm <= 1e-12 * max(psi0, np.linalg.norm(Pn)):
                 break
             du, it = condensation.condensed_solve(d, uk, psi, b1, 1e-12)
             its.append(it)
