@@ -412,6 +412,15 @@ sdme_status sdme_mass_solve(sdme_ctx* ctx, const double* b_dev, double* x_dev, d
 /* The context's Q = P + 2 Gauss-Legendre points and weights on [-1, 1] (host arrays, may be NULL). */
 sdme_status sdme_gauss_points(const sdme_ctx* ctx, double* xq, double* wq);
 
+/*
+ * Physical coordinates of the Gauss points (the affine map of each box
+ * element, eq. ProdTensorialHexaedro with the trilinear geometry):
+ * X_dev[(e Q^3 + q) 3 + d], e and q ordered as for sdme_body_load; a
+ * float64 device array of nelem Q^3 3 entries, caller-owned, overwritten.
+ * Stream-ordered, no synchronisation.  SDME_EUNSUPPORTED for 2D contexts.
+ */
+sdme_status sdme_gauss_point_coords(sdme_ctx* ctx, double* X_dev);
+
 /* Cumulative device event timings of the context (ms) and counts, for measurement. */
 typedef struct {
   double tangent_ms;     /* sum of timed tangent-kernel launches */
@@ -424,6 +433,7 @@ const char* sdme_cuda_error_string(const sdme_ctx* ctx);
 
 /* Enable (1) / disable (0) CUDA-event timing of every tangent-kernel launch. */
 sdme_status sdme_set_timing(sdme_ctx* ctx, int enable);
+sdme_status sdme_get_timing(sdme_ctx* ctx, sdme_timing* out);
 
 /*
  * MIXED_FP32 contexts: the largest number of float64-residual restarts
@@ -433,7 +443,6 @@ sdme_status sdme_set_timing(sdme_ctx* ctx, int enable);
  * SDME_EINVAL for a negative count.
  */
 sdme_status sdme_set_refinement(sdme_ctx* ctx, int max_restarts);
-sdme_status sdme_get_timing(sdme_ctx* ctx, sdme_timing* out);
 
 /*
  * y_dev = (b1 M + K_T(u)) x_dev in float64, like sdme_tangent_apply, but
@@ -444,11 +453,13 @@ sdme_status sdme_get_timing(sdme_ctx* ctx, sdme_timing* out);
  * allocations, or while other work must not be disturbed by allocator
  * synchronisation.
  *
- * Inputs: mesh, material and order P (1..8) as for sdme_create; the 1D
- * tables xq[Q], wq[Q], B[Q*(P+1)], D[Q*(P+1)] with Q = P + 2, exactly as
- * sdme_build_basis1d returns them (host arrays, read during the call);
- * u_dev (linearisation point), x_dev, y_dev: float64 device vectors of
- * length 3 Nn.  Constrained DOFs get y = x, as in sdme_tangent_apply.
+ * Inputs: a hexahedral mesh, material and order P (1..8) as for
+ * sdme_create (three-dimensional meshes only: nelem[2] = 0 returns
+ * SDME_EINVAL); the 1D tables xq[Q], wq[Q], B[Q*(P+1)], D[Q*(P+1)] with
+ * Q = P + 2, exactly as sdme_build_basis1d returns them (host arrays, read
+ * during the call); u_dev (linearisation point), x_dev, y_dev: float64
+ * device vectors of length 3 Nn.  Constrained DOFs get y = x, as in
+ * sdme_tangent_apply.
  *
  * Scratch: the linearisation state and the discarded internal-force vector
  * live in one static device array of 2^21 float64 words (16 MiB) that every
@@ -458,9 +469,12 @@ sdme_status sdme_get_timing(sdme_ctx* ctx, sdme_timing* out);
  * call clears what must start at zero.  Calls that overlap on the GPU (for
  * example on two streams at once) race on the array and must be avoided.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  The call synchronises `stream` (NULL = legacy
- * default stream) to report SDME_NONPOSITIVE_J.
+ * (cudaGetSymbolAddress) with that device current and keeps it for later
+ * calls on that device; make that first call before any stream capture.
+ * The kept address assumes that the device's context lives as long as the
+ * process: after a cudaDeviceReset the array must be looked up again, which
+ * this entry point does not do.  The call synchronises `stream` (NULL =
+ * legacy default stream) to report SDME_NONPOSITIVE_J.
  */
 sdme_status sdme_tangent_apply_noalloc(const sdme_mesh_desc* mesh, const sdme_material* mat, int P,
                                        const double* xq, const double* wq, const double* B, const double* D,

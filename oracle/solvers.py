@@ -4,7 +4,8 @@
   the paper's CGD / element-by-element diagonal PCG (Sec. 5, Conrod;
   conclusions).  Stopping rule (reading; the paper gives only tolerances):
   ||r||_2 <= rtol ||b||_2 on the unpreconditioned residual, x0 = 0.
-* ``dense_solve``: direct solve of the assembled system (tiny meshes).
+* ``dense_solve`` / ``sparse_solve``: direct solve of the assembled system
+  (dense LU for tiny meshes, scipy's sparse LU for small ones).
 * ``newmark_step``: one implicit Newmark step solved by Newton-Raphson
   (Sec. 4.2, eqs. Eq:residual, NR_explicit).  The paper's coefficient table
   for the Newmark approximations is garbled; the reading is the standard
@@ -51,6 +52,12 @@ def dense_solve(A, b):
     return np.linalg.solve(A, b)
 
 
+def sparse_solve(A, b):
+    """Direct solve of the assembled sparse system (scipy's sparse LU)."""
+    import scipy.sparse.linalg as spla
+    return spla.spsolve(A.tocsc(), b)
+
+
 def _newton(disc, u, residual_fn, b1, tol, pcg_rtol, maxnewton, linear, pload_norm, stats):
     mask = disc.mask
     psi0 = None
@@ -68,6 +75,9 @@ def _newton(disc, u, residual_fn, b1, tol, pcg_rtol, maxnewton, linear, pload_no
             break
         if linear == "direct":
             du = dense_solve(disc.tangent_matrix(u, b1), psi)
+            stats["pcg_iters"].append(0)
+        elif linear == "sparse":
+            du = sparse_solve(disc.tangent_matrix(u, b1), psi)
             stats["pcg_iters"].append(0)
         else:
             d = disc.diagonal(u, b1)

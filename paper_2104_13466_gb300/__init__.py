@@ -37,7 +37,7 @@ EXPORTS = ("sdme_status_string", "sdme_build_basis1d", "sdme_create", "sdme_dest
            "sdme_explicit_forward", "sdme_explicit_adjoint", "sdme_batch_create", "sdme_batch_destroy",
            "sdme_batch_layout", "sdme_batch_internal_force", "sdme_batch_tangent_apply", "sdme_batch_traction_load",
            "sdme_batch_newmark_step", "sdme_batch_tune", "sdme_batch_launches", "sdme_static_solve",
-           "sdme_set_condensation", "sdme_set_refinement")
+           "sdme_set_condensation", "sdme_set_refinement", "sdme_gauss_point_coords")
 
 
 class BasisDesc(ctypes.Structure):
@@ -139,6 +139,7 @@ def _load():
     lib.sdme_set_condensation.argtypes = [vp, i]
     lib.sdme_set_timing.argtypes = [vp, i]
     lib.sdme_set_refinement.argtypes = [vp, i]
+    lib.sdme_gauss_point_coords.argtypes = [vp, vp]
     lib.sdme_get_timing.argtypes = [vp, ctypes.POINTER(Timing)]
     lib.sdme_tangent_apply_noalloc.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(Material), i, pd, pd, pd,
                                                pd, vp, d, vp, vp, vp]
@@ -399,20 +400,16 @@ class Context:
                                      wq.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "sdme_gauss_points")
         return xq, wq
 
-    def gauss_point_coords(self, elems, lengths):
-        """Physical coordinates (torch, float64, [nelem][Q^3][3]) of the Gauss
-        points in the layout sdme_body_load expects (host-side helper)."""
-        import numpy as np
+    def gauss_point_coords(self, elems=None, lengths=None):
+        """Physical coordinates (torch CUDA float64, [nelem][Q^3][3]) of the
+        Gauss points in the layout sdme_body_load expects
+        (sdme_gauss_point_coords; the mesh is the context's own, the
+        arguments are accepted for compatibility and ignored)."""
         import torch
-        xq, _ = self.gauss_points()
         Q = self.P + 2
-        h = [lengths[d] / elems[d] for d in range(3)]
-        k3, k2, k1 = np.meshgrid(np.arange(Q), np.arange(Q), np.arange(Q), indexing="ij")
-        ref = np.stack([xq[k1.ravel()], xq[k2.ravel()], xq[k3.ravel()]], axis=-1)     # (Q3, 3)
-        ez, ey, ex = np.meshgrid(np.arange(elems[2]), np.arange(elems[1]), np.arange(elems[0]), indexing="ij")
-        org = np.stack([ex.ravel() * h[0], ey.ravel() * h[1], ez.ravel() * h[2]], axis=-1)  # (E, 3)
-        X = org[:, None, :] + 0.5 * (1.0 + ref[None, :, :]) * np.array(h)[None, None, :]
-        return torch.from_numpy(X)
+        X = torch.empty((self.nelem, Q ** 3, 3), dtype=torch.float64, device="cuda")
+        _check(lib.sdme_gauss_point_coords(self._h, _ptr(X)), "sdme_gauss_point_coords", ctx=self._h)
+        return X
 
     def body_load(self, fq, f):
         return _check(lib.sdme_body_load(self._h, _ptr(fq), _ptr(f)), "sdme_body_load", ctx=self._h)

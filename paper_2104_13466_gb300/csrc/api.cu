@@ -2,6 +2,7 @@
 // the Newton-Newmark driver.  All device work goes through the element
 // kernels (elem_p<P>.cu) and the per-DOF kernels (vec_kernels.cuh).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdio>
@@ -42,6 +43,34 @@ constexpr int64_t kDeferMaxElems = 8192;
     sdme_status s_ = (call);        \
     if (s_ != SDME_OK) return s_;   \
   } while (0)
+
+// NVTX range over a host scope (phases of a solve, seen by nsys / ncu
+// --nvtx when a tool is attached; a no-op otherwise).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
+// Physical coordinates of the Gauss points, [nelem][Q^3][3].
+struct GaussCoordParams {
+  double xq[16];
+  double h[3];
+  int ne[3];
+  int Q;
+};
+
+__global__ void k_gauss_coords(GaussCoordParams p, int64_t total, double* __restrict__ X) {
+  const int Q3 = p.Q * p.Q * p.Q;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / Q3;
+    const int q = (int)(i - e * Q3);
+    const int k1 = q % p.Q, k2 = (q / p.Q) % p.Q, k3 = q / (p.Q * p.Q);
+    const int ex = (int)(e % p.ne[0]), ey = (int)((e / p.ne[0]) % p.ne[1]), ez = (int)(e / ((int64_t)p.ne[0] * p.ne[1]));
+    X[3 * i + 0] = p.h[0] * (ex + 0.5 * (1.0 + p.xq[k1]));
+    X[3 * i + 1] = p.h[1] * (ey + 0.5 * (1.0 + p.xq[k2]));
+    X[3 * i + 2] = p.h[2] * (ez + 0.5 * (1.0 + p.xq[k3]));
+  }
+}
 
 }  // namespace
 
@@ -315,6 +344,7 @@ sdme_status residual64(sdme_ctx* ctx, double b1, int op, const double* b, const 
 template <typename T, typename TV>
 sdme_status pcg_core(sdme_ctx* ctx, double b1, int op, const double* b, double* x, double rtol, int maxit,
                      int* iters, double* rel, TV* r, TV* p, TV* q, TV* dinv, double* xv) {
+  NvtxRange range_pcg("sdme pcg");
   SideStreamScope scope(ctx);
   if (op == kOpMass) {
     SDME_CUDA(cudaMemsetAsync(dinv, 0, sizeof(TV) * ctx->ndof, ctx->stream));
@@ -325,6 +355,7 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, int op, const double* b, double* 
     SDME_CUDA(cudaGetLastError());
     ctx->kernel_launches += 2;
   } else if (op == kOpTangent) {
+    NvtxRange range_diag("sdme diagonal");
     SDME_TRY(diag_launch<T>(ctx, b1, (T*)dinv, 1));
   }  // kOpCondensed: the caller has put 1 / diag(S) in dinv
   k_pcg_init<TV, double><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, b, 1.0, dinv, xv, r, p, q,
@@ -347,6 +378,7 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, int op, const double* b, double* 
       cudaGraphExecDestroy(ge);
       ge = nullptr;
     }
+    NvtxRange range_chunk("sdme pcg chunk (operator, update, direction)");
     if (tim) {
       SDME_TRY((pcg_chunk<T, TV>(ctx, b1, op, true, r, p, q, dinv, xv)));
     } else if (!ge) {
@@ -396,7 +428,10 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, int op, const double* b, double* 
       double rr64 = 0.0;
       const double bb = s.bb;
       const int it = s.iter;
-      SDME_TRY(residual64(ctx, b1, op, b, xv, &rr64));
+      {
+        NvtxRange range_ref("sdme refinement residual (float64 operator)");
+        SDME_TRY(residual64(ctx, b1, op, b, xv, &rr64));
+      }
       const double prev = true_rel;
       true_rel = bb > 0.0 ? std::sqrt(rr64 / bb) : 0.0;
       if (!std::isfinite(true_rel)) return SDME_NAN;
@@ -638,7 +673,10 @@ sdme_status newton_core(sdme_ctx* ctx, double* u, const double* P_next_dev, doub
   double psi0 = -1.0, nrm_prev = -1.0, eta_prev = 0.01, ref = 0.0;
   sdme_status result = SDME_NEWTON_DIVERGED;
   for (int k = 0; k <= o.max_newton; ++k) {
-    SDME_TRY(residual_launch(ctx, b1, u, ctx->y));
+    {
+      NvtxRange range_res("sdme residual");
+      SDME_TRY(residual_launch(ctx, b1, u, ctx->y));
+    }
     k_residual_combine<<<kVecBlocks, kVecThreads, 0, s>>>(ctx->mi, P_next_dev, mhat, ctx->y, ctx->psi,
                                                         ctx->partial, ctx->dcount, ctx->dscal);
     SDME_CUDA(cudaGetLastError());
@@ -752,15 +790,22 @@ sdme_status sdme_create(sdme_ctx** out, const sdme_mesh_desc* mesh, const sdme_m
   // nelem[2] == 0: a plane-strain mesh of quadrilaterals in the x-y plane
   const int dim = mesh->nelem[2] == 0 ? 2 : 3;
   for (int d = 0; d < dim; ++d)
-    if (mesh->nelem[d] < 1 || !(mesh->length[d] > 0.0)) return SDME_EINVAL;
+    if (mesh->nelem[d] < 1 || mesh->nelem[d] > (1 << 24) || !(mesh->length[d] > 0.0) ||
+        !std::isfinite(mesh->length[d]))
+      return SDME_EINVAL;
   if (dim == 2 && (mesh->clamp[4] != 0 || mesh->clamp[5] != 0 || basis->kind == SDME_NODAL_LUMPED))
     return SDME_EINVAL;
-  if (!(mat->mu > 0.0) || !(mat->lambda >= 0.0) || !(mat->rho >= 0.0)) return SDME_EINVAL;
+  if (!(mat->mu > 0.0) || !(mat->lambda >= 0.0) || !(mat->rho >= 0.0) || !std::isfinite(mat->mu) ||
+      !std::isfinite(mat->lambda) || !std::isfinite(mat->rho))
+    return SDME_EINVAL;
   const int P = basis->P, n = P + 1, Q = P + 2;
   int64_t N[3];
   for (int d = 0; d < 3; ++d) N[d] = (d < dim) ? (int64_t)mesh->nelem[d] * P + 1 : 1;
+  // element and DOF counts bounded in floating point first (no integer overflow)
+  if ((double)mesh->nelem[0] * mesh->nelem[1] * (dim == 3 ? mesh->nelem[2] : 1) > 2147483647.0 ||
+      3.0 * (double)N[0] * (double)N[1] * (double)N[2] > (double)((int64_t)1 << 40))
+    return SDME_EINVAL;
   const int64_t nelem = (int64_t)mesh->nelem[0] * mesh->nelem[1] * (dim == 3 ? mesh->nelem[2] : 1);
-  if (nelem > 0x7fffffff || N[0] * N[1] * N[2] * 3 > ((int64_t)1 << 40)) return SDME_EINVAL;
 
   sdme_ctx* ctx = new (std::nothrow) sdme_ctx();
   if (!ctx) return SDME_ENOMEM;
@@ -1321,6 +1366,25 @@ sdme_status sdme_gauss_points(const sdme_ctx* ctx, double* xq, double* wq) {
     if (xq) xq[q] = x[q];
     if (wq) wq[q] = w[q];
   }
+  return SDME_OK;
+}
+
+sdme_status sdme_gauss_point_coords(sdme_ctx* ctx, double* X_dev) {
+  if (!ctx || !X_dev) return SDME_EINVAL;
+  if (ctx->h.dim != 3) return SDME_EUNSUPPORTED;
+  GaussCoordParams p{};
+  std::vector<double> x(ctx->Q), w(ctx->Q);
+  gauss_legendre(ctx->Q, x.data(), w.data());
+  for (int q = 0; q < ctx->Q; ++q) p.xq[q] = x[q];
+  for (int d = 0; d < 3; ++d) {
+    p.h[d] = ctx->mesh.length[d] / ctx->mesh.nelem[d];
+    p.ne[d] = ctx->mesh.nelem[d];
+  }
+  p.Q = ctx->Q;
+  const int64_t total = (int64_t)ctx->h.nelem * ctx->Q * ctx->Q * ctx->Q;
+  k_gauss_coords<<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(p, total, X_dev);
+  SDME_CUDA(cudaGetLastError());
+  ctx->kernel_launches += 1;
   return SDME_OK;
 }
 

@@ -8,6 +8,7 @@
 // performs no host or device allocation.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "../../include/sdme.h"
@@ -103,6 +104,11 @@ sdme_status run(const sdme_mesh_desc* mesh, const sdme_material* mat, const doub
     N[d] = (int64_t)mesh->nelem[d] * P + 1;
     prm.N[d] = (int)N[d];
   }
+  // sizes bounded in floating point first (no integer overflow for any mesh)
+  if (3.0 * (double)N[0] * (double)N[1] * (double)N[2] +
+          (double)mesh->nelem[0] * mesh->nelem[1] * mesh->nelem[2] * kStateFields * Q3 >
+      (double)(kScratchWords - kHeaderWords))
+    return SDME_EINVAL;
   prm.detJ = h[0] * h[1] * h[2] / 8.0;
   prm.mu = mat->mu;
   prm.lam = mat->lambda;
@@ -113,7 +119,7 @@ sdme_status run(const sdme_mesh_desc* mesh, const sdme_material* mat, const doub
   const int64_t nelem = (int64_t)mesh->nelem[0] * mesh->nelem[1] * mesh->nelem[2];
   const int64_t ndof = 3 * prm.Nn;
   const int64_t state_words = nelem * kStateFields * Q3;
-  if (nelem > 0x7fffffff || (uint64_t)(kHeaderWords + ndof + state_words) > kScratchWords) return SDME_EINVAL;
+  if ((uint64_t)(kHeaderWords + ndof + state_words) > kScratchWords) return SDME_EINVAL;
 
   double* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return SDME_ECUDA;
@@ -153,9 +159,14 @@ extern "C" sdme_status sdme_tangent_apply_noalloc(const sdme_mesh_desc* mesh, co
                                                   const double* D, const double* u_dev, double b1,
                                                   const double* x_dev, double* y_dev, void* stream) {
   if (!mesh || !mat || !xq || !wq || !B || !D || !u_dev || !x_dev || !y_dev) return SDME_EINVAL;
+  // hexahedral meshes only (nelem[2] = 0, a plane-strain mesh, is rejected here)
   for (int d = 0; d < 3; ++d)
-    if (mesh->nelem[d] < 1 || !(mesh->length[d] > 0.0)) return SDME_EINVAL;
-  if (!(mat->mu > 0.0) || !(mat->lambda >= 0.0) || !(mat->rho >= 0.0)) return SDME_EINVAL;
+    if (mesh->nelem[d] < 1 || mesh->nelem[d] > (1 << 24) || !(mesh->length[d] > 0.0) ||
+        !std::isfinite(mesh->length[d]))
+      return SDME_EINVAL;
+  if (!(mat->mu > 0.0) || !(mat->lambda >= 0.0) || !(mat->rho >= 0.0) || !std::isfinite(mat->mu) ||
+      !std::isfinite(mat->lambda) || !std::isfinite(mat->rho))
+    return SDME_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   switch (P) {
     case 1: return run<1>(mesh, mat, xq, wq, B, D, u_dev, b1, x_dev, y_dev, s);

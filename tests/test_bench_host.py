@@ -71,3 +71,6 @@ def test_flop_model_figures():
     assert abs(plain / bench.tangent_flops_per_element(8) - 1.46) < 0.01
     # the nodal basis pays the pairing adds on the mode-side lines
     assert bench.tangent_flops_per_element(8, nodal=True) > bench.tangent_flops_per_element(8)
+    # the roofline's unit is the plain count: 859,680 flops per P = 8 element
+    assert bench.algorithmic_flops_per_element(8) == plain == 859680
+    assert bench.algorithmic_flops_per_element(8) * 4096 == 3521249280

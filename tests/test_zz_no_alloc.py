@@ -7,6 +7,10 @@ static device array inside the library.  Its result must equal the
 context-based sdme_tangent_apply to the float64 tolerance used everywhere
 else (1e-10 relative), on consecutive calls that share that array.
 
+The result is also checked against the FP64 oracle's effective tangent
+(Sec. 3, consistent linearisation) at P = 8, the largest order, on a mesh
+that fits the array.
+
 This file is collected last on purpose, so that a failure here does not stop
 a first-failure run before the other tests have run.
 """
@@ -30,9 +34,9 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
 
 
-def _call_noalloc(s, P, tables, mu, lam, rho, u, b1, x, y):
+def _call_noalloc(s, P, tables, mu, lam, rho, u, b1, x, y, elems=ELEMS, lengths=LENGTHS, clamp=CLAMP):
     # straight through the C ABI
-    mesh = s.mesh_desc(ELEMS, LENGTHS, CLAMP)
+    mesh = s.mesh_desc(elems, lengths, clamp)
     mat = s.Material(mu, lam, rho)
     arrs = [np.ascontiguousarray(t, dtype=np.float64) for t in tables]
     ptrs = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs]
@@ -68,6 +72,32 @@ def test_noalloc_tangent_matches_context_tangent_twice(P, kind):
     ctx.close()
 
 
+def test_noalloc_tangent_matches_oracle_at_p8():
+    import paper_2104_13466_gb300 as s
+    from oracle.assembly import Discretization
+    from oracle.basis1d import Basis1D
+    from oracle.hexmesh import BoxMesh
+    P, kind = 8, "sdme_h"
+    elems, lengths = (2, 2, 1), (1.0, 0.8, 0.6)
+    clamp = {"xmin": (0, 1, 2)}
+    mu, lam = lame(1000.0, 0.45)
+    rho = 1.0
+    mesh = BoxMesh(*elems, P, lengths).clamp("xmin")
+    disc = Discretization(mesh, Basis1D(P, kind), mu, lam, rho)
+    xq, wq, B, D, _, _ = s.build_basis1d(P, kind)
+    for seed, b1 in ((21, 4.0), (22, 0.0)):
+        u = random_vector(mesh.ndof, seed, 0.02 * 0.6 / P)
+        x = random_vector(mesh.ndof, seed + 100)
+        y = torch.full((mesh.ndof,), float("nan"), dtype=torch.float64, device="cuda")
+        st = _call_noalloc(s, P, (xq, wq, B, D), mu, lam, rho, _dev(u), b1, _dev(x), y, elems, lengths, clamp)
+        assert st == s.OK
+        torch.cuda.synchronize()
+        want = disc.effective_apply(u, x, b1)
+        got = y.cpu().numpy()
+        err = np.abs(got - want).max() / np.abs(want).max()
+        assert err < TOL64, (seed, err)
+
+
 def test_noalloc_rejects_problems_beyond_its_scratch():
     import paper_2104_13466_gb300 as s
     mu, lam = lame(1000.0, 0.3)
@@ -79,6 +109,13 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     arrs = [np.ascontiguousarray(t, dtype=np.float64) for t in (xq, wq, B, D)]
     ptrs = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs]
     st = s.lib.sdme_tangent_apply_noalloc(ctypes.byref(big), ctypes.byref(mat), P, *ptrs,
+                                          ctypes.c_void_p(one.data_ptr()), ctypes.c_double(0.0),
+                                          ctypes.c_void_p(one.data_ptr()), ctypes.c_void_p(one.data_ptr()),
+                                          ctypes.c_void_p(0))
+    assert st == s.EINVAL
+    # plane-strain meshes (nelem[2] = 0) are not served by this entry point
+    flat = s.mesh_desc((2, 2), (1.0, 1.0), {})
+    st = s.lib.sdme_tangent_apply_noalloc(ctypes.byref(flat), ctypes.byref(mat), P, *ptrs,
                                           ctypes.c_void_p(one.data_ptr()), ctypes.c_double(0.0),
                                           ctypes.c_void_p(one.data_ptr()), ctypes.c_void_p(one.data_ptr()),
                                           ctypes.c_void_p(0))
