@@ -466,7 +466,7 @@ def run_gpu(args, w):
     e3.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e2.elapsed_time(e3)
-    e2e_value = ws * n * e2e_mv / (e2e_ms * 1e-3) if e2e_ms > 0 and e2e_conv else None
+    e2e_value = ws * n * e2e_mv / (e2e_ms * 1e-3) if args.e2e_steps > 0 and e2e_ms > 0 and e2e_conv else None
     ctx.close()
 
     cpu = None
@@ -854,8 +854,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--basis", default="sdme_h",
-                    choices=["nodal", "modal", "sdme_m", "sdme_k", "sdme_h", "nodal_lumped"])
+    ap.add_argument("--basis", default=None,
+                    choices=["nodal", "modal", "sdme_m", "sdme_k", "sdme_h", "nodal_lumped"],
+                    help="default: the workload's basis (sdme_k for the quasi-static cantilever, else sdme_h)")
     ap.add_argument("--workload", default="beam_p8")
     ap.add_argument("--mixed-rtol", type=float, default=1e-4)
     ap.add_argument("--pcg-maxit", type=int, default=20000)
@@ -872,7 +873,7 @@ def main():
     ap.add_argument("--bases", default="nodal,modal,sdme_m,sdme_h")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the basis / precision / unit-cube comparisons printed beside the default line")
-    ap.add_argument("--compare-bases", default="nodal,modal,sdme_m,sdme_k")
+    ap.add_argument("--compare-bases", default="nodal,modal,sdme_m,sdme_k,sdme_h")
     ap.add_argument("--compare-levels", type=int, default=5)
     ap.add_argument("--precisions", default="mixed,fp64")
     ap.add_argument("--kernel-iters", type=int, default=20)
@@ -892,6 +893,8 @@ def main():
     if args.explicit and args.workload == "beam_p8":
         args.workload = "cube_p6_explicit"
     w = workload(args.workload)
+    if args.basis is None:
+        args.basis = w.get("basis", "sdme_h")
     if args.batch:
         run_batch(args, w)
     elif args.adjoint:

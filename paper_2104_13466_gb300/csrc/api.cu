@@ -102,11 +102,12 @@ struct sdme_ctx {
   int upd_blocks[2] = {kVecBlocks, kVecBlocks}, dir_blocks[2] = {kVecBlocks, kVecBlocks};
   double* dscal = nullptr;      // [0]: norm^2 results ; counters follow
   unsigned int* dcount = nullptr;
-  // PCG vectors (x64: the solution, float64 in both precisions; in a
-  // MIXED_FP32 context r64 and q64 hold the refinement's float64 residual
-  // and operator product)
+  // PCG vectors (x64: the solution of a float64 solve; in a MIXED_FP32
+  // context x64, r64 and q64 hold the refinement's float64 solution,
+  // residual and operator product)
   double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr, *d64 = nullptr, *x64 = nullptr;
   float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
+  float *xh32 = nullptr, *xl32 = nullptr;   // MIXED_FP32: the solution as a float32 pair (hi + lo)
   // iterative refinement of the float32 PCG (MIXED_FP32): at most this many
   // restarts from the float64 residual per solve (0: off), and the outcome
   // of the last solve
@@ -251,7 +252,7 @@ enum PcgOp { kOpTangent = 0, kOpMass = 1, kOpCondensed = 2 };
 
 // Issue one chunk of PCG iterations (operator, update, direction) on ctx->stream.
 template <typename T, typename TV>
-sdme_status pcg_chunk(sdme_ctx* ctx, double b1, int op, bool tim, TV* r, TV* p, TV* q, TV* dinv, double* xv) {
+sdme_status pcg_chunk(sdme_ctx* ctx, double b1, int op, bool tim, TV* r, TV* p, TV* q, TV* dinv, TV* xh, TV* xl) {
   // hexahedral tangent / mass operators leave p.(A p) as per-element
   // partials for the update kernel (no last-CTA finalize in the operator)
   const bool defer = op != kOpCondensed && ctx->h.dim == 3 && ctx->h.nelem <= kDeferMaxElems;
@@ -277,10 +278,11 @@ sdme_status pcg_chunk(sdme_ctx* ctx, double b1, int op, bool tim, TV* r, TV* p, 
                                       tim ? ctx->ev[2 * j + 1] : nullptr, defer)));
     }
     constexpr int vi = sizeof(TV) == 4 ? 1 : 0;
-    k_pcg_update<TV, double><<<ctx->upd_blocks[vi], kVecThreads, 0, ctx->stream>>>(
-        ctx->ndof, xv, r, p, q, dinv, ctx->scal, ctx->partial + ctx->upart_off, defer ? ctx->partial : nullptr,
+    k_pcg_update<TV><<<ctx->upd_blocks[vi], kVecThreads, 0, ctx->stream>>>(
+        ctx->ndof, r, q, dinv, ctx->scal, ctx->partial + ctx->upart_off, defer ? ctx->partial : nullptr,
         (int)ctx->h.nelem);
-    k_pcg_direction<TV><<<ctx->dir_blocks[vi], kVecThreads, 0, ctx->stream>>>(ctx->ndof, r, dinv, p, ctx->scal);
+    k_pcg_direction<TV><<<ctx->dir_blocks[vi], kVecThreads, 0, ctx->stream>>>(ctx->ndof, r, dinv, p, xh, xl,
+                                                                             ctx->scal);
   }
   SDME_CUDA(cudaGetLastError());
   return SDME_OK;
@@ -329,7 +331,7 @@ sdme_status residual64(sdme_ctx* ctx, double b1, int op, const double* b, const 
 
 // Jacobi PCG on (b1 M + K_T) with the linearisation state already stored.
 // b and x are float64 device vectors; the iteration runs in TV / T with the
-// solution accumulated in float64 (xv).  The iterations are issued in chunks
+// solution accumulated in xh (float64) or in the float32 pair xh + xl.  The iterations are issued in chunks
 // of kPcgChunk captured once as a CUDA graph (kernels see the device-side
 // status and return at once after convergence); the host reads the status
 // between chunks.
@@ -343,7 +345,7 @@ sdme_status residual64(sdme_ctx* ctx, double b1, int op, const double* b, const 
 // float64 operator, as a float64 solve would.
 template <typename T, typename TV>
 sdme_status pcg_core(sdme_ctx* ctx, double b1, int op, const double* b, double* x, double rtol, int maxit,
-                     int* iters, double* rel, TV* r, TV* p, TV* q, TV* dinv, double* xv) {
+                     int* iters, double* rel, TV* r, TV* p, TV* q, TV* dinv, TV* xh, TV* xl) {
   NvtxRange range_pcg("sdme pcg");
   SideStreamScope scope(ctx);
   if (op == kOpMass) {
@@ -358,8 +360,8 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, int op, const double* b, double* 
     NvtxRange range_diag("sdme diagonal");
     SDME_TRY(diag_launch<T>(ctx, b1, (T*)dinv, 1));
   }  // kOpCondensed: the caller has put 1 / diag(S) in dinv
-  k_pcg_init<TV, double><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, b, 1.0, dinv, xv, r, p, q,
-                                                                      ctx->scal, ctx->partial, rtol, maxit);
+  k_pcg_init<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->mi, b, 1.0, dinv, xh, xl, r, p, q, ctx->scal,
+                                                              ctx->partial, rtol, maxit);
   SDME_CUDA(cudaGetLastError());
   ctx->kernel_launches += 1;
   const bool refine = sizeof(TV) == 4 && ctx->refine_max > 0 && (op == kOpTangent || op == kOpMass);
@@ -380,14 +382,14 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, int op, const double* b, double* 
     }
     NvtxRange range_chunk("sdme pcg chunk (operator, update, direction)");
     if (tim) {
-      SDME_TRY((pcg_chunk<T, TV>(ctx, b1, op, true, r, p, q, dinv, xv)));
+      SDME_TRY((pcg_chunk<T, TV>(ctx, b1, op, true, r, p, q, dinv, xh, xl)));
     } else if (!ge) {
       // first chunk runs directly (also sets the kernels' attributes), then
       // the same chunk is captured for the following ones
-      SDME_TRY((pcg_chunk<T, TV>(ctx, b1, op, false, r, p, q, dinv, xv)));
+      SDME_TRY((pcg_chunk<T, TV>(ctx, b1, op, false, r, p, q, dinv, xh, xl)));
       cudaGraph_t g = nullptr;
       SDME_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-      sdme_status cs = pcg_chunk<T, TV>(ctx, b1, op, false, r, p, q, dinv, xv);
+      sdme_status cs = pcg_chunk<T, TV>(ctx, b1, op, false, r, p, q, dinv, xh, xl);
       cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
       if (cs != SDME_OK) return cs;
       SDME_CUDA(ce);
@@ -424,13 +426,22 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, int op, const double* b, double* 
     }
     done_iters = s.iter;
     if (s.status == kPcgRunning) continue;
+    if (s.status == kPcgConverged || s.status == kPcgMaxit) {
+      // the last iteration's x += alpha p (its direction kernel returned at once)
+      k_pcg_xfinal<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, p, xh, xl, ctx->scal);
+      SDME_CUDA(cudaGetLastError());
+      ctx->kernel_launches += 1;
+    }
     if (refine && s.status == kPcgConverged) {
       double rr64 = 0.0;
       const double bb = s.bb;
       const int it = s.iter;
       {
         NvtxRange range_ref("sdme refinement residual (float64 operator)");
-        SDME_TRY(residual64(ctx, b1, op, b, xv, &rr64));
+        k_pcg_xout<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, xh, xl, ctx->x64);
+        SDME_CUDA(cudaGetLastError());
+        ctx->kernel_launches += 1;
+        SDME_TRY(residual64(ctx, b1, op, b, ctx->x64, &rr64));
       }
       const double prev = true_rel;
       true_rel = bb > 0.0 ? std::sqrt(rr64 / bb) : 0.0;
@@ -451,8 +462,11 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, int op, const double* b, double* 
   ctx->last_sweeps = sweeps;
   ctx->last_true_rel = true_rel;
   if (rel) *rel = true_rel >= 0.0 ? true_rel : ((s.bb > 0.0) ? std::sqrt(s.rr / s.bb) : 0.0);
-  if (x != xv)
-    SDME_CUDA(cudaMemcpyAsync(x, xv, sizeof(double) * ctx->ndof, cudaMemcpyDeviceToDevice, ctx->stream));
+  if ((void*)x != (void*)xh) {
+    k_pcg_xout<TV><<<kVecBlocks, kVecThreads, 0, ctx->stream>>>(ctx->ndof, xh, xl, x);
+    SDME_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 1;
+  }
   if (s.status == kPcgBreakdown) return SDME_NAN;
   if (s.status == kPcgMaxit) return SDME_PCG_MAXIT;
   return SDME_OK;
@@ -463,9 +477,9 @@ sdme_status pcg_dispatch(sdme_ctx* ctx, double b1, const double* b, double* x, d
   const int op = mass_only ? kOpMass : kOpTangent;
   if (ctx->prec == SDME_MIXED_FP32)
     return pcg_core<float, float>(ctx, b1, op, b, x, rtol, maxit, iters, rel, ctx->r32, ctx->p32, ctx->q32,
-                                  ctx->d32, ctx->x64);
+                                  ctx->d32, ctx->xh32, ctx->xl32);
   return pcg_core<double, double>(ctx, b1, op, b, x, rtol, maxit, iters, rel, ctx->r64, ctx->p64, ctx->q64,
-                                  ctx->d64, ctx->x64);
+                                  ctx->d64, ctx->x64, nullptr);
 }
 
 // M x = b on the free DOFs (x = 0 on constrained ones): Jacobi-PCG on the
@@ -515,7 +529,7 @@ sdme_status cond_solve(sdme_ctx* ctx, double b1, const double* f, double* x, dou
   for (int v : errs)
     if (v) return SDME_NAN;  // interior block not positive definite
   const sdme_status ps = pcg_core<double, double>(ctx, b1, kOpCondensed, ctx->cg, x, rtol, maxit, iters, rel,
-                                                  ctx->r64, ctx->p64, ctx->q64, ctx->d64, ctx->x64);
+                                                  ctx->r64, ctx->p64, ctx->q64, ctx->d64, ctx->x64, nullptr);
   if (ps != SDME_OK && ps != SDME_PCG_MAXIT) return ps;
   cond_recover_kernel<<<ne, 256, sizeof(double) * (Ni + Nb), s>>>(Ni, Nb, ctx->cgI, ctx->cgB, ctx->cL, ctx->cW,
                                                                   ctx->cY, x);
@@ -573,6 +587,7 @@ sdme_status dot_host(sdme_ctx* ctx, const double* x, const double* y, double* ou
 void free_all(sdme_ctx* ctx) {
   void* dev[] = {ctx->st64, ctx->st32, ctx->err, ctx->scal, ctx->partial, ctx->dscal, ctx->dcount,
                  ctx->r64, ctx->p64, ctx->q64, ctx->d64, ctx->x64, ctx->r32, ctx->p32, ctx->q32, ctx->d32,
+                 ctx->xh32, ctx->xl32,
                  ctx->un, ctx->ahat, ctx->mhat, ctx->y, ctx->psi, ctx->du, ctx->mlump,
                  ctx->cIl, ctx->cBl, ctx->cerr, ctx->cgI, ctx->cgB, ctx->cKe, ctx->cL, ctx->cW, ctx->cS,
                  ctx->cY, ctx->cg, ctx->loc};
@@ -898,7 +913,8 @@ sdme_status sdme_create(sdme_ctx** out, const sdme_mesh_desc* mesh, const sdme_m
     ok = ok && dalloc(&ctx->r32, nd) == cudaSuccess && dalloc(&ctx->p32, nd) == cudaSuccess &&
          dalloc(&ctx->q32, nd) == cudaSuccess && dalloc(&ctx->d32, nd) == cudaSuccess &&
          dalloc(&ctx->x64, nd) == cudaSuccess && dalloc(&ctx->r64, nd) == cudaSuccess &&
-         dalloc(&ctx->q64, nd) == cudaSuccess;
+         dalloc(&ctx->q64, nd) == cudaSuccess && dalloc(&ctx->xh32, nd) == cudaSuccess &&
+         dalloc(&ctx->xl32, nd) == cudaSuccess;
   } else {
     ok = ok && dalloc(&ctx->r64, nd) == cudaSuccess && dalloc(&ctx->p64, nd) == cudaSuccess &&
          dalloc(&ctx->q64, nd) == cudaSuccess && dalloc(&ctx->d64, nd) == cudaSuccess &&
@@ -933,8 +949,7 @@ sdme_status sdme_create(sdme_ctx** out, const sdme_mesh_desc* mesh, const sdme_m
       *out = std::max(1, std::min(kVecBlocks, per_sm * sms));
       return true;
     };
-    ok = ok && wave(k_pcg_update<double, double>, &ctx->upd_blocks[0]) &&
-         wave(k_pcg_update<float, double>, &ctx->upd_blocks[1]) &&
+    ok = ok && wave(k_pcg_update<double>, &ctx->upd_blocks[0]) && wave(k_pcg_update<float>, &ctx->upd_blocks[1]) &&
          wave(k_pcg_direction<double>, &ctx->dir_blocks[0]) && wave(k_pcg_direction<float>, &ctx->dir_blocks[1]);
   }
   if (ok && basis->kind == SDME_NODAL_LUMPED) ok = build_lumped_mass(ctx) == SDME_OK;

@@ -8,7 +8,10 @@
 namespace sdme {
 
 // Linearisation state layout per element: [10][Q^3]: H = F^{-T} (9, row
-// major iJ) then c = mu - lambda ln J.
+// major iJ) then c = mu - lambda ln J.  The float32 copy holds
+// Ht_cd = sqrt(w_q detJ) s_d H_cd in place of H (w_q the product of the
+// Gauss weights, s_d = 2 / h_d), so that the quadrature weight and the
+// reference-to-physical derivative scales fold into the tangent action.
 constexpr int kStateFields = 10;
 
 // PCG status values held in PcgScalars::status

@@ -608,6 +608,7 @@ __device__ __forceinline__ void residual_body(const ElemTables<double, P>& tb, i
     const T wdet = tb.W[qx] * tb.W[qy] * tb.W[qz] * m.detJ;
     const T a = m.lam * lnJ;
     const T cst = m.mu - a;
+    const T rw = st32 ? sqrt(wdet) : T(0);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -617,7 +618,9 @@ __device__ __forceinline__ void residual_body(const ElemTables<double, P>& tb, i
         sm[(3 + 3 * d + c) * FQ + so] = wdet * Pcd * sc[d];
         const int64_t o = ((int64_t)e * kStateFields + (c * 3 + d)) * Q3 + q;
         if (st64) st64[o] = H;
-        if (st32) st32[o] = (float)H;
+        // float32 state: H scaled by the square root of the quadrature
+        // weight and by the derivative scale of its column
+        if (st32) st32[o] = (float)(rw * sc[d] * H);
       }
     const int64_t o = ((int64_t)e * kStateFields + 9) * Q3 + q;
     if (st64) st64[o] = cst;
@@ -698,7 +701,63 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
       }
     }
   }
-  for (int q = threadIdx.x; STIFF && q < Q3; q += NT) {
+  if constexpr (STIFF && sizeof(T) == 4) {
+    // Scaled float32 state Ht = sqrt(w detJ) H diag(s) (see kStateFields):
+    // with the reference gradient G (dF = G diag(s)) the weighted flux
+    // w detJ dP diag(s) is  mu w detJ s_j^2 G_ij + c (Ht G^T Ht)_ij
+    // + lambda (Ht : G) Ht_ij, and its contraction with G is the element
+    // quadrature form of dF : dP.
+    const T mus2[3] = {m.mu * m.detJ * sc[0] * sc[0], m.mu * m.detJ * sc[1] * sc[1],
+                       m.mu * m.detJ * sc[2] * sc[2]};
+    const T b1rho = m.b1 * m.rho * m.detJ;
+    for (int q = threadIdx.x; q < Q3; q += NT) {
+      const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
+      const int so = (qz * Q + qy) * XQ + qx;
+      T H[3][3], Gr[3][3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          H[c][d] = ste[(c * 3 + d) * Q3 + q];
+          Gr[c][d] = sm[(3 + 3 * d + c) * FQ + so];
+        }
+      const T cst = ste[9 * Q3 + q];
+      T tr = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) tr += H[c][d] * Gr[c][d];
+      T W[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) W[a][j] = Gr[0][a] * H[0][j] + Gr[1][a] * H[1][j] + Gr[2][a] * H[2][j];
+      const T w = tb.W[qx] * tb.W[qy] * tb.W[qz];
+      const T ltr = m.lam * tr;
+      T qf = T(0);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const T mw = w * mus2[j];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const T V = H[i][0] * W[0][j] + H[i][1] * W[1][j] + H[i][2] * W[2][j];
+          const T fl = mw * Gr[i][j] + cst * V + ltr * H[i][j];
+          sm[(3 + 3 * j + i) * FQ + so] = fl;
+          if (QDOT) qf += Gr[i][j] * fl;
+        }
+      }
+      const T mfac = b1rho * w;
+      T mq = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T u = sm[c * FQ + so];
+        sm[c * FQ + so] = u * mfac;
+        if (QDOT) mq += u * u;
+      }
+      if (QDOT) dotq += (double)(qf + mfac * mq);
+    }
+  }
+  for (int q = threadIdx.x; STIFF && sizeof(T) == 8 && q < Q3; q += NT) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
     const int so = (qz * Q + qy) * XQ + qx;
     T H[3][3], dF[3][3];
@@ -929,10 +988,19 @@ __device__ __forceinline__ void diag_body(const ElemTables<T, P>& tb, const Mesh
 #pragma unroll
       for (int f = 0; f < 6; ++f) {
         const int d = fd[f], d2 = fe[f];
-        T v = a * h[d] * h[d2];
-        if (d == d2) v += m.mu;
-        else v *= T(2);
-        F7[f * Q3 + q] = wdet * sc[d] * sc[d2] * v;
+        if constexpr (sizeof(T) == 4) {
+          // scaled float32 state (see kStateFields): h_d h_d2 already
+          // carries wdet s_d s_d2
+          T v = a * h[d] * h[d2];
+          if (d == d2) v += wdet * sc[d] * sc[d] * m.mu;
+          else v *= T(2);
+          F7[f * Q3 + q] = v;
+        } else {
+          T v = a * h[d] * h[d2];
+          if (d == d2) v += m.mu;
+          else v *= T(2);
+          F7[f * Q3 + q] = wdet * sc[d] * sc[d2] * v;
+        }
       }
       F7[6 * Q3 + q] = m.b1 * m.rho * wdet;
     }

@@ -109,15 +109,20 @@ __global__ void __launch_bounds__(kVecThreads) k_axpy(int64_t n, double alpha, c
 }
 
 //----------------------------------------------------------------------------
-// Jacobi PCG (CGD).  Vectors r, p, q, dinv in TV (dinv = 1 / diag); the
-// solution x in TX (float64 for both precisions: a float32 x would bound
-// the float64 residual b - A x at about eps32 |A| |x|).
+// Jacobi PCG (CGD).  Vectors r, p, q, dinv in TV (dinv = 1 / diag).  The
+// solution x is float64 (TV = double) or, with float32 vectors, a float32
+// pair (hi, lo) holding hi + lo to about 48 bits: a float32 x would bound the
+// float64 residual b - A x at about eps32 |A| |x|, and float64 arithmetic
+// runs at a small fraction of the float32 rate on GB300.
 //   init:      r = scale*b (0 on constrained), x = 0, q = 0, p = z = dinv r,
 //              rz = r.z, bb = r.r
 //   per iteration:  tangent kernel: q = A p, pq = p.q, alpha = rz / pq
-//                   update:    x += alpha p, r -= alpha q, q = 0,
+//                   update:    r -= alpha q, q = 0,
 //                              rz' = r.(dinv r), rr = r.r, test, beta = rz'/rz
-//                   direction: p = dinv r + beta p
+//                   direction: x += alpha p (with the p the operator saw),
+//                              p = dinv r + beta p
+//   final:     after the iteration that meets the test (the direction kernel
+//              then returns at once) the host issues x += alpha p.
 //   restart:   r = a given float64 residual, p = z = dinv r (x, bb, tol2 and
 //              the iteration count kept): the refinement step of the float32
 //              solve.
@@ -125,11 +130,11 @@ __global__ void __launch_bounds__(kVecThreads) k_axpy(int64_t n, double alpha, c
 // summed four at a time, one 16-byte vector), accumulated per thread and
 // reduced across threads in float64.
 //----------------------------------------------------------------------------
-template <typename TV, typename TX>
+template <typename TV>
 __global__ void __launch_bounds__(kVecThreads) k_pcg_init(MeshInfo mi, const double* __restrict__ b, double scale,
-                                                          const TV* __restrict__ dinv, TX* __restrict__ x,
-                                                          TV* __restrict__ r, TV* __restrict__ p,
-                                                          TV* __restrict__ q, PcgScalars* scal,
+                                                          const TV* __restrict__ dinv, TV* __restrict__ xh,
+                                                          TV* __restrict__ xl, TV* __restrict__ r,
+                                                          TV* __restrict__ p, TV* __restrict__ q, PcgScalars* scal,
                                                           double* __restrict__ partial, double rtol, int maxit) {
   double srz = 0.0, srr = 0.0;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < mi.ndof;
@@ -138,7 +143,8 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_init(MeshInfo mi, const dou
     const TV z = dinv[g] * rv;
     r[g] = rv;
     p[g] = z;
-    x[g] = TX(0);
+    xh[g] = TV(0);
+    if (xl) xl[g] = TV(0);
     q[g] = TV(0);
     srz += (double)(rv * z);
     srr += (double)(rv * rv);
@@ -192,15 +198,50 @@ __device__ __forceinline__ auto& lane(V& v, int i) {
   return reinterpret_cast<typename std::remove_reference<decltype(v.x)>::type*>(&v)[i];
 }
 
-// W consecutive entries of the solution vector (16 or 32 bytes).
-template <typename TX, int W>
-struct alignas(sizeof(TX) * W) XPack {
-  TX v[W];
-};
+// (hi, lo) += a * v for a float32 pair: the product split exactly by an FMA
+// (Dekker / Ogita-Rump-Oishi TwoProduct), its high part added by Knuth's
+// TwoSum, the low parts folded in and the pair renormalised.  The _rn
+// intrinsics keep the compiler from fusing or reassociating the steps.
+__device__ __forceinline__ void pair_axpy(float& hi, float& lo, float a, float v) {
+  const float ph = __fmul_rn(a, v);
+  const float pl = __fmaf_rn(a, v, -ph);
+  const float s = __fadd_rn(hi, ph);
+  const float bv = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(ph, bv));
+  const float t = __fadd_rn(e, __fadd_rn(lo, pl));
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
 
-template <typename TV, typename TX>
-__global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TX* __restrict__ x, TV* __restrict__ r,
-                                                            const TV* __restrict__ p, TV* __restrict__ q,
+// x += alpha p (alpha from the scalars): the solution update of the
+// iteration whose direction kernel returned at once (the test was met).
+template <typename TV>
+__global__ void __launch_bounds__(kVecThreads) k_pcg_xfinal(int64_t n, const TV* __restrict__ p,
+                                                            TV* __restrict__ xh, TV* __restrict__ xl,
+                                                            const PcgScalars* scal) {
+  const double alpha = scal->alpha;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(TV) == 4) {
+      float h = xh[g], l = xl[g];
+      pair_axpy(h, l, (float)alpha, p[g]);
+      xh[g] = h;
+      xl[g] = l;
+    } else {
+      xh[g] += alpha * p[g];
+    }
+  }
+}
+
+// out = hi + lo in float64 (TV = float), or a copy of x (TV = double).
+template <typename TV>
+__global__ void __launch_bounds__(kVecThreads) k_pcg_xout(int64_t n, const TV* __restrict__ xh,
+                                                          const TV* __restrict__ xl, double* __restrict__ out) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    out[g] = xl ? (double)xh[g] + (double)xl[g] : (double)xh[g];
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TV* __restrict__ r, TV* __restrict__ q,
                                                             const TV* __restrict__ dinv, PcgScalars* scal,
                                                             double* __restrict__ partial,
                                                             const double* __restrict__ dot_partial = nullptr,
@@ -208,19 +249,15 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TX* __res
   if (scal->status != kPcgRunning) return;
   using V = typename Vec16<TV>::type;
   constexpr int W = Vec16<TV>::width;
-  using XP = XPack<TX, W>;
   const int64_t nv = n / W;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   // the first chunk's loads do not depend on the step length: issue them
   // before it is summed so that their latency overlaps the sum
-  XP x0;
-  V r0, p0, q0, d0;
+  V r0, q0, d0;
   const bool first = t0 < nv;
   if (first) {
-    x0 = reinterpret_cast<const XP*>(x)[t0];
     r0 = reinterpret_cast<const V*>(r)[t0];
-    p0 = reinterpret_cast<const V*>(p)[t0];
     q0 = reinterpret_cast<const V*>(q)[t0];
     d0 = reinterpret_cast<const V*>(dinv)[t0];
   }
@@ -242,13 +279,11 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TX* __res
     alpha_d = scal->alpha;
   }
   const TV alpha = (TV)alpha_d;
-  const TX alpha_x = (TX)alpha_d;
   double srz = 0.0, srr = 0.0;
-  auto body = [&](XP& xv, V& rv, V& pv, V& qv, V& dv, int64_t g) {
+  auto body = [&](V& rv, V& qv, V& dv, int64_t g) {
     TV vrz = TV(0), vrr = TV(0);
 #pragma unroll
     for (int i = 0; i < W; ++i) {
-      xv.v[i] += alpha_x * (TX)lane(pv, i);
       const TV ri = lane(rv, i) - alpha * lane(qv, i);
       lane(rv, i) = ri;
       vrz += ri * (lane(dv, i) * ri);
@@ -256,42 +291,35 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TX* __res
     }
     srz += (double)vrz;
     srr += (double)vrr;
-    reinterpret_cast<XP*>(x)[g] = xv;
     reinterpret_cast<V*>(r)[g] = rv;
     reinterpret_cast<V*>(q)[g] = V{};
   };
   int64_t g = t0;
   if (first) {
-    body(x0, r0, p0, q0, d0, t0);
+    body(r0, q0, d0, t0);
     g += stride;
   }
-  // two chunks per trip (ten 16-byte loads in flight per thread), same
-  // chunk order as a one-chunk loop
+  // two chunks per trip (six 16-byte loads in flight per thread), same chunk
+  // order as a one-chunk loop
   for (; g + stride < nv; g += 2 * stride) {
-    XP xv[2];
-    V rv[2], pv[2], qv[2], dv[2];
+    V rv[2], qv[2], dv[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      xv[u] = reinterpret_cast<const XP*>(x)[g + u * stride];
       rv[u] = reinterpret_cast<const V*>(r)[g + u * stride];
-      pv[u] = reinterpret_cast<const V*>(p)[g + u * stride];
       qv[u] = reinterpret_cast<const V*>(q)[g + u * stride];
       dv[u] = reinterpret_cast<const V*>(dinv)[g + u * stride];
     }
 #pragma unroll
-    for (int u = 0; u < 2; ++u) body(xv[u], rv[u], pv[u], qv[u], dv[u], g + u * stride);
+    for (int u = 0; u < 2; ++u) body(rv[u], qv[u], dv[u], g + u * stride);
   }
   for (; g < nv; g += stride) {
-    XP xv = reinterpret_cast<const XP*>(x)[g];
     V rv = reinterpret_cast<const V*>(r)[g];
-    V pv = reinterpret_cast<const V*>(p)[g];
     V qv = reinterpret_cast<const V*>(q)[g];
     V dv = reinterpret_cast<const V*>(dinv)[g];
-    body(xv, rv, pv, qv, dv, g);
+    body(rv, qv, dv, g);
   }
   for (int64_t g = nv * W + t0; g < n; g += stride) {  // tail
     const TV qv = q[g];
-    x[g] += alpha_x * (TX)p[g];
     const TV rv = r[g] - alpha * qv;
     r[g] = rv;
     q[g] = TV(0);
@@ -327,11 +355,14 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TX* __res
 template <typename TV>
 __global__ void __launch_bounds__(kVecThreads) k_pcg_direction(int64_t n, const TV* __restrict__ r,
                                                                const TV* __restrict__ dinv, TV* __restrict__ p,
+                                                               TV* __restrict__ xh, TV* __restrict__ xl,
                                                                const PcgScalars* scal) {
   if (scal->status != kPcgRunning) return;
   using V = typename Vec16<TV>::type;
   constexpr int W = Vec16<TV>::width;
   const TV beta = (TV)scal->beta;
+  const double alpha_d = scal->alpha;
+  const TV alpha = (TV)alpha_d;
   const int64_t nv = n / W;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -339,11 +370,33 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_direction(int64_t n, const 
     V rv = reinterpret_cast<const V*>(r)[g];
     V dv = reinterpret_cast<const V*>(dinv)[g];
     V pv = reinterpret_cast<const V*>(p)[g];
+    V hv = reinterpret_cast<const V*>(xh)[g];
+    if constexpr (sizeof(TV) == 4) {
+      V lv = reinterpret_cast<const V*>(xl)[g];
+#pragma unroll
+      for (int i = 0; i < W; ++i) pair_axpy(lane(hv, i), lane(lv, i), alpha, lane(pv, i));
+      reinterpret_cast<V*>(xl)[g] = lv;
+    } else {
+#pragma unroll
+      for (int i = 0; i < W; ++i) lane(hv, i) += alpha * lane(pv, i);
+    }
+    reinterpret_cast<V*>(xh)[g] = hv;
 #pragma unroll
     for (int i = 0; i < W; ++i) lane(pv, i) = lane(dv, i) * lane(rv, i) + beta * lane(pv, i);
     reinterpret_cast<V*>(p)[g] = pv;
   }
-  for (int64_t g = nv * W + t0; g < n; g += stride) p[g] = dinv[g] * r[g] + beta * p[g];
+  for (int64_t g = nv * W + t0; g < n; g += stride) {
+    const TV pg = p[g];
+    if constexpr (sizeof(TV) == 4) {
+      float h = xh[g], l = xl[g];
+      pair_axpy(h, l, alpha, pg);
+      xh[g] = h;
+      xl[g] = l;
+    } else {
+      xh[g] += alpha * pg;
+    }
+    p[g] = dinv[g] * r[g] + beta * pg;
+  }
 }
 
 template <typename TV>
