@@ -842,7 +842,8 @@ def run_batch(args, w):
            "newton_iters_mean": float(np.mean(newton)), "newton_iters_max": int(np.max(newton)),
            "pcg_iters_per_newton_mean": float(np.mean(pcg)), "pcg_iters_per_newton_max": float(np.max(pcg)),
            "gpu_launches": launches, "create_s": t_create,
-           "tuning": [{"P": p_, "grid": g_, "tangent_ms": m_} for p_, g_, m_ in tuning]}
+           "tuning": [{"P": p_, "grid": g_, "tangent_ms": m_} for p_, g_, m_ in tuning],
+           "persistent": b.persistent_info()}
     b.close()
     print(json.dumps(out), flush=True)
 

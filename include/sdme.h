@@ -546,9 +546,41 @@ sdme_status sdme_batch_newmark_step(sdme_batch* b, sdme_state* state, double dt,
  * step).  orders/grids/ms (ngroups_max entries each, may be NULL) receive
  * each group's order, chosen grid (0 = one CTA per element) and time per
  * launch; *ngroups the number of groups.
+ * Unless the persistent form is switched off (sdme_batch_set_persistent),
+ * the tuner then times the PCG operator as one persistent launch across
+ * all order groups: for each order the number of elements a work item
+ * holds (1 up to 4, as many as 320 threads allow: one group of
+ * 3 (P+2)^2 threads, rounded up to whole warps, per element), then the
+ * whole batch with those tiles, and keeps the persistent launch for the
+ * PCG iterations when it beats the sum of the per-order launches.
  */
 sdme_status sdme_batch_tune(sdme_batch* b, int reps, int ngroups_max, int* ngroups, int* orders, int* grids,
                             float* ms);
+
+/*
+ * The PCG operator of a batch as one persistent launch across all order
+ * groups (the benchmark spec's batching form): CTAs of 320 threads claim work items
+ * (up to kper[P] consecutive elements of one problem of order P, one group
+ * of threads per element) from a device counter until none is left; each
+ * problem's last element to finish sums the problem's step-length partials.
+ * No CTA waits on another.  mode: 1 always, 0 never (one launch per order
+ * group), -1 (the default) as sdme_batch_tune decides.  kper (host, 9
+ * entries indexed by P, may be NULL to keep the current ones): elements per
+ * work item for each order, 1 up to min(4, 320 / threads per element)
+ * (threads per element: 3 (P+2)^2 rounded up to a multiple of 32), else
+ * SDME_EINVAL; the tuner overwrites them.  Setting the mode drops the
+ * captured PCG graph.  SDME_EINVAL for another mode.
+ */
+sdme_status sdme_batch_set_persistent(sdme_batch* b, int mode, const int* kper);
+
+/*
+ * The persistent form's state: *on (1 when the PCG iterations use it),
+ * kper[9] (elements per work item by order, index = P), the tuner's time
+ * of one persistent launch over the whole batch and the sum of the
+ * per-order launch times (ms, -1 before tuning).  Any pointer may be NULL.
+ */
+sdme_status sdme_batch_persistent_info(const sdme_batch* b, int* on, int kper[9], float* persist_ms,
+                                       float* groups_ms);
 
 /* Kernel launches issued by the batch so far (all kinds). */
 sdme_status sdme_batch_launches(const sdme_batch* b, int64_t* launches);

@@ -37,7 +37,8 @@ EXPORTS = ("sdme_status_string", "sdme_build_basis1d", "sdme_create", "sdme_dest
            "sdme_explicit_forward", "sdme_explicit_adjoint", "sdme_batch_create", "sdme_batch_destroy",
            "sdme_batch_layout", "sdme_batch_internal_force", "sdme_batch_tangent_apply", "sdme_batch_traction_load",
            "sdme_batch_newmark_step", "sdme_batch_tune", "sdme_batch_launches", "sdme_static_solve",
-           "sdme_set_condensation", "sdme_set_refinement", "sdme_gauss_point_coords")
+           "sdme_set_condensation", "sdme_set_refinement", "sdme_gauss_point_coords", "sdme_batch_set_persistent",
+           "sdme_batch_persistent_info")
 
 
 class BasisDesc(ctypes.Structure):
@@ -140,6 +141,9 @@ def _load():
     lib.sdme_set_timing.argtypes = [vp, i]
     lib.sdme_set_refinement.argtypes = [vp, i]
     lib.sdme_gauss_point_coords.argtypes = [vp, vp]
+    lib.sdme_batch_set_persistent.argtypes = [vp, i, ctypes.POINTER(i)]
+    lib.sdme_batch_persistent_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float),
+                                               ctypes.POINTER(ctypes.c_float)]
     lib.sdme_get_timing.argtypes = [vp, ctypes.POINTER(Timing)]
     lib.sdme_tangent_apply_noalloc.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(Material), i, pd, pd, pd,
                                                pd, vp, d, vp, vp, vp]
@@ -661,3 +665,21 @@ class Batch:
         n = ctypes.c_int64()
         _check(lib.sdme_batch_launches(self._h, ctypes.byref(n)), "sdme_batch_launches")
         return n.value
+
+    def set_persistent(self, mode, kper=None):
+        """PCG operator as one persistent launch across the order groups:
+        mode 1 always, 0 never, -1 as the tuner decides; kper: {P: elements
+        per work item} (orders not given keep 1)."""
+        arr = None
+        if kper is not None:
+            arr = (ctypes.c_int * 9)(*[int(kper.get(P, 1)) if P else 0 for P in range(9)])
+        return _check(lib.sdme_batch_set_persistent(self._h, int(mode), arr), "sdme_batch_set_persistent")
+
+    def persistent_info(self):
+        on = ctypes.c_int()
+        kper = (ctypes.c_int * 9)()
+        pm, gm = ctypes.c_float(), ctypes.c_float()
+        _check(lib.sdme_batch_persistent_info(self._h, ctypes.byref(on), kper, ctypes.byref(pm), ctypes.byref(gm)),
+               "sdme_batch_persistent_info")
+        return {"on": bool(on.value), "kper": {P: kper[P] for P in range(1, 9)}, "persist_ms": pm.value,
+                "groups_ms": gm.value}

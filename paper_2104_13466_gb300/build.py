@@ -18,7 +18,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 GXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-I" + INCLUDE]
 
-CU_SOURCES = ["api.cu", "noalloc.cu", "batch.cu"] + ["elem_p%d.cu" % p for p in range(1, 9)]
+CU_SOURCES = ["api.cu", "noalloc.cu", "batch.cu", "batch_persist.cu"] + ["elem_p%d.cu" % p for p in range(1, 9)]
 CPP_SOURCES = ["basis1d.cpp"]
 
 

@@ -3,6 +3,9 @@
 // every element operation is one launch per group (up to 128 problems per
 // launch), every per-DOF operation one launch for the whole batch, and the
 // PCG iterations of all problems run as one captured CUDA graph per chunk.
+// The PCG operator can instead run as one persistent launch across all
+// order groups (batch_persist.cuh), with the elements per work item chosen
+// per order by the tuner; the tuner keeps whichever form is faster.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -107,6 +110,17 @@ struct sdme_batch {
   std::vector<int> grun;      // running problems the captured chunk was built for
   bool warm = false;          // kernels' attributes set (first chunk ran directly)
   int64_t launches = 0;
+  // cross-order persistent PCG operator
+  int persist_mode = -1;      // -1: the tuner decides, 0: per-order launches, 1: persistent
+  bool persist_on = false;
+  int kper[9] = {0, 1, 1, 1, 1, 1, 1, 1, 1};
+  float persist_ms = -1.f, groups_ms = -1.f;
+  int persist_grid = 0;
+  double persist_b1 = -1.0;   // b1 of the uploaded per-problem table
+  PersistItem* items = nullptr;
+  int* nitems = nullptr;
+  int* queue = nullptr;
+  unsigned char* pprobs = nullptr;
 };
 
 #define B_CUDA(call)                 \
@@ -127,7 +141,8 @@ struct sdme_batch {
 namespace {
 
 void batch_free(sdme_batch* b) {
-  void* dev[] = {b->info, b->cta_prob, b->active, b->err, b->scal, b->partial, b->dcount, b->dnorm,
+  void* dev[] = {b->items, b->nitems, b->queue, b->pprobs,
+                 b->info, b->cta_prob, b->active, b->err, b->scal, b->partial, b->dcount, b->dnorm,
                  b->st64, b->st32, b->r64, b->p64, b->q64, b->d64, b->x64, b->r32, b->p32, b->q32,
                  b->d32, b->x32, b->un, b->ahat, b->mhat, b->y, b->psi, b->du, b->loc};
   for (void* p : dev)
@@ -201,6 +216,81 @@ template <typename T>
 const T* b_state(sdme_batch* b) {
   if constexpr (sizeof(T) == 8) return b->st64;
   else return b->st32;
+}
+
+// The persistent launch's view of the batch: each order's tables and tile.
+HostPersist b_persist_desc(sdme_batch* b) {
+  HostPersist hp;
+  for (Group& g : b->groups) {
+    hp.tabs[g.P] = &g.tabs;
+    hp.kper[g.P] = b->kper[g.P];
+  }
+  return hp;
+}
+
+// Uploads the work items for the problems in `run` (all when null), largest
+// order first, kper[P] consecutive elements per item, and the per-problem
+// table when b1 changed.  Stream-ordered on the batch's stream.
+sdme_status b_persist_items(sdme_batch* b, const std::vector<int>* run, double b1, int only_P = 0) {
+  std::vector<int> order;
+  if (run) order = *run;
+  else
+    for (int i = 0; i < b->nprob; ++i) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->probs[a].P > b->probs[c].P; });
+  std::vector<PersistItem> items;
+  for (int i : order) {
+    const Prob& pr = b->probs[i];
+    if (only_P && pr.P != only_P) continue;
+    const int K = std::max(1, b->kper[pr.P]);
+    for (int64_t e = 0; e < pr.nelem; e += K)
+      items.push_back(PersistItem{pr.P, i, (int)e, (int)std::min<int64_t>(K, pr.nelem - e)});
+  }
+  const int n = (int)items.size();
+  if (n > 0)
+    B_CUDA(cudaMemcpyAsync(b->items, items.data(), sizeof(PersistItem) * n, cudaMemcpyHostToDevice, b->stream));
+  B_CUDA(cudaMemcpyAsync(b->nitems, &n, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  if (b->persist_b1 != b1) {
+    std::vector<HostPersistProb> hp(b->nprob);
+    for (int i = 0; i < b->nprob; ++i) {
+      const Prob& pr = b->probs[i];
+      hp[i].mesh = pr.hm;
+      hp[i].dof_off = pr.off;
+      hp[i].st_off = pr.st_off;
+      hp[i].part_off = pr.part_off;
+      hp[i].pid = i;
+      hp[i].nelem = (int)pr.nelem;
+    }
+    std::vector<unsigned char> img;
+    if (b->prec == SDME_MIXED_FP32) persist_probs_image<float>(hp, b1, img);
+    else persist_probs_image<double>(hp, b1, img);
+    B_CUDA(cudaMemcpyAsync(b->pprobs, img.data(), img.size(), cudaMemcpyHostToDevice, b->stream));
+    b->persist_b1 = b1;
+  }
+  // the pageable sources must stay valid until the copies have run
+  B_CUDA(cudaStreamSynchronize(b->stream));
+  return SDME_OK;
+}
+
+template <typename T, typename TV>
+sdme_status b_persist_launch(sdme_batch* b, const TV* x, TV* y, double* partial, PcgScalars* scal) {
+  B_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream));
+  const HostPersist hp = b_persist_desc(b);
+  B_CUDA((launch_batch_persistent<T, TV>(hp, b->persist_grid, b->items, b->nitems, b->queue, b->pprobs, x, y,
+                                          b_state<T>(b), partial, scal, b->stream)));
+  b->launches += 1;
+  return SDME_OK;
+}
+
+sdme_status b_persist_grid(sdme_batch* b) {
+  const HostPersist hp = b_persist_desc(b);
+  const int occ = b->prec == SDME_MIXED_FP32 ? persist_occupancy<float, float>(hp)
+                                             : persist_occupancy<double, double>(hp);
+  int dev = 0, sms = 0;
+  B_CUDA(cudaGetDevice(&dev));
+  B_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (occ < 1) return SDME_ECUDA;
+  b->persist_grid = occ * sms;
+  return SDME_OK;
 }
 
 template <typename T, typename TV>
@@ -299,7 +389,8 @@ struct BatchSideScope {
 template <typename T, typename TV>
 sdme_status b_pcg_chunk(sdme_batch* b, double b1, TV* r, TV* p, TV* q, TV* dinv, TV* xv) {
   for (int j = 0; j < kChunk; ++j) {
-    B_TRY((b_tangent<T, TV>(b, b1, p, q, b->partial, b->scal, true)));
+    if (b->persist_on) B_TRY((b_persist_launch<T, TV>(b, p, q, b->partial, b->scal)));
+    else B_TRY((b_tangent<T, TV>(b, b1, p, q, b->partial, b->scal, true)));
     kb_pcg_update<TV><<<b->vec_grid, kVecThreads, 0, b->stream>>>(b->info, b->cta_prob, xv, r, p, q, dinv, b->scal,
                                                                   b->partial);
     kb_pcg_direction<TV><<<b->vec_grid, kVecThreads, 0, b->stream>>>(b->info, b->cta_prob, r, dinv, p, b->scal);
@@ -341,6 +432,10 @@ sdme_status b_pcg(sdme_batch* b, double b1, const double* rhs, double* x_out, do
         b->gexec = nullptr;
       }
       build_run_launches(b, run);
+      if (b->persist_on) {
+        if (!b->persist_grid) B_TRY(b_persist_grid(b));
+        B_TRY(b_persist_items(b, &run, b1));
+      }
       if (!b->warm) {  // the first chunk runs directly (sets the kernels' attributes)
         B_TRY((b_pcg_chunk<T, TV>(b, b1, r, p, q, dinv, xv)));
         b->warm = true;
@@ -364,7 +459,9 @@ sdme_status b_pcg(sdme_batch* b, double b1, const double* rhs, double* x_out, do
     }
     B_CUDA(cudaGraphLaunch(b->gexec, b->stream));
     int64_t per = 2 * kChunk;
-    for (const Group& g : b->groups) per += kChunk * (int64_t)g.run_launches.size();
+    if (b->persist_on) per += kChunk;
+    else
+      for (const Group& g : b->groups) per += kChunk * (int64_t)g.run_launches.size();
     b->launches = l0 + per;
     B_TRY(read_status(run));
   }
@@ -513,6 +610,10 @@ sdme_status sdme_batch_create(sdme_batch** out, const sdme_problem* probs, int n
   ok = ok && dalloc(&b->un, nt) == cudaSuccess && dalloc(&b->ahat, nt) == cudaSuccess &&
        dalloc(&b->mhat, nt) == cudaSuccess && dalloc(&b->y, nt) == cudaSuccess &&
        dalloc(&b->psi, nt) == cudaSuccess && dalloc(&b->du, nt) == cudaSuccess;
+  ok = ok && dalloc(&b->items, (size_t)b->nelem_total) == cudaSuccess && dalloc(&b->nitems, 1) == cudaSuccess &&
+       dalloc(&b->queue, 1) == cudaSuccess &&
+       dalloc(&b->pprobs, np * (prec == SDME_MIXED_FP32 ? persist_prob_bytes<float>()
+                                                         : persist_prob_bytes<double>())) == cudaSuccess;
   ok = ok && cudaMallocHost((void**)&b->scal_h, sizeof(PcgScalars) * np) == cudaSuccess &&
        cudaMallocHost((void**)&b->dnorm_h, sizeof(double) * np) == cudaSuccess &&
        cudaMallocHost((void**)&b->err_h, sizeof(int) * np) == cudaSuccess &&
@@ -561,6 +662,8 @@ sdme_status sdme_batch_create(sdme_batch** out, const sdme_problem* probs, int n
         for (HostBatchLaunch& L : g.launches)
           for (size_t k = 0; ok && k < L.pid.size(); ++k)
             if (toff[L.pid[k]] >= 0) L.mesh[k].loc = b->loc + toff[L.pid[k]];
+      for (size_t i = 0; ok && i < np; ++i)
+        if (toff[i] >= 0) b->probs[i].hm.loc = b->loc + toff[i];
     }
   }
   if (!ok) {
@@ -757,6 +860,37 @@ sdme_status sdme_batch_newmark_step(sdme_batch* b, sdme_state* state, double dt,
   return out;
 }
 
+sdme_status sdme_batch_set_persistent(sdme_batch* b, int mode, const int* kper) {
+  if (!b || mode < -1 || mode > 1) return SDME_EINVAL;
+  if (kper)
+    for (int P = 1; P <= kMaxP; ++P) {
+      const int nt = (3 * (P + 2) * (P + 2) + 31) / 32 * 32;
+      if (kper[P] < 1 || kper[P] > std::min(kPersistMaxTile, 320 / nt)) return SDME_EINVAL;
+    }
+  if (kper)
+    for (int P = 1; P <= kMaxP; ++P) b->kper[P] = kper[P];
+  b->persist_mode = mode;
+  b->persist_on = mode == 1;
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  b->grun.clear();
+  b->persist_grid = 0;
+  return SDME_OK;
+}
+
+sdme_status sdme_batch_persistent_info(const sdme_batch* b, int* on, int kper[9], float* persist_ms,
+                                       float* groups_ms) {
+  if (!b) return SDME_EINVAL;
+  if (on) *on = b->persist_on ? 1 : 0;
+  if (kper)
+    for (int P = 0; P <= 8; ++P) kper[P] = b->kper[P];
+  if (persist_ms) *persist_ms = b->persist_ms;
+  if (groups_ms) *groups_ms = b->groups_ms;
+  return SDME_OK;
+}
+
 sdme_status sdme_batch_tune(sdme_batch* b, int reps, int ngroups_max, int* ngroups, int* orders, int* grids,
                             float* ms) {
   if (!b || reps < 1) return SDME_EINVAL;
@@ -816,6 +950,52 @@ sdme_status sdme_batch_tune(sdme_batch* b, int reps, int ngroups_max, int* ngrou
     if (result != SDME_OK) break;
   }
   if (ngroups) *ngroups = (int)b->groups.size();
+  // the cross-order persistent operator: elements per item for each order
+  // (timed on that order's problems alone), then the whole batch in one
+  // launch against the sum of the per-order launches
+  b->groups_ms = 0.f;
+  for (const Group& g : b->groups) b->groups_ms += g.tuned_ms;
+  if (result == SDME_OK && b->persist_mode != 0) {
+    const bool mixed = b->prec == SDME_MIXED_FP32;
+    auto time_persist = [&](float* out) -> sdme_status {
+      // every problem running, counters at zero (the next PCG initialises them again)
+      B_CUDA(cudaMemsetAsync(b->scal, 0, sizeof(PcgScalars) * b->nprob, b->stream));
+      float t = 0.f;
+      for (int r = -1; r < reps; ++r) {
+        if (r == 0) B_CUDA(cudaEventRecord(e0, b->stream));
+        B_TRY((mixed ? b_persist_launch<float, float>(b, b->p32, b->q32, b->partial, b->scal)
+                     : b_persist_launch<double, double>(b, b->p64, b->q64, b->partial, b->scal)));
+      }
+      B_CUDA(cudaEventRecord(e1, b->stream));
+      B_CUDA(cudaEventSynchronize(e1));
+      B_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      *out = t / reps;
+      return SDME_OK;
+    };
+    for (Group& g : b->groups) {
+      const int nt = (3 * (g.P + 2) * (g.P + 2) + 31) / 32 * 32;
+      const int kmax = std::max(1, std::min(kPersistMaxTile, 320 / nt));
+      float best = -1.f;
+      int bestk = 1;
+      for (int k = 1; k <= kmax && result == SDME_OK; ++k) {
+        b->kper[g.P] = k;
+        float t = 0.f;
+        result = b_persist_grid(b);
+        if (result == SDME_OK) result = b_persist_items(b, nullptr, 0.0, g.P);
+        if (result == SDME_OK) result = time_persist(&t);
+        if (result == SDME_OK && (best < 0.f || t < best)) {
+          best = t;
+          bestk = k;
+        }
+      }
+      b->kper[g.P] = bestk;
+    }
+    if (result == SDME_OK) result = b_persist_grid(b);
+    if (result == SDME_OK) result = b_persist_items(b, nullptr, 0.0);
+    if (result == SDME_OK) result = time_persist(&b->persist_ms);
+    b->persist_on = result == SDME_OK && (b->persist_mode == 1 || b->persist_ms < b->groups_ms);
+    b->persist_b1 = -1.0;   // rebuilt with the solve's b1
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   // the tuning launches wrote into q: clear it for the next PCG

@@ -38,7 +38,7 @@ cond_columns_kernel(const __grid_constant__ ElemParams<double, P> prm, const dou
     jcons = cons;
   }
   __syncthreads();
-  tangent_core<P, T, true>(prm.tab, prm.pairs, m, e, st, sm);
+  tangent_core<P, T, true>(prm.tab, prm.pairs, m, e, st, sm, threadIdx.x);
   double* col = Ke + ((int64_t)e * N + j) * N;
   for (int idx = threadIdx.x; idx < N; idx += blockDim.x) {
     bool cons;

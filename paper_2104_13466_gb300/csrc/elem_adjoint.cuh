@@ -38,7 +38,7 @@ vjp_kernel(const __grid_constant__ ElemParams<double, P> prm, const double* __re
     X[so] = w[g];
   }
   __syncthreads();
-  forward_stages<T, P, true>(prm.tab, prm.pairs, sm);
+  forward_stages<T, P, true>(prm.tab, prm.pairs, sm, threadIdx.x);
   const T sc[3] = {prm.s[0], prm.s[1], prm.s[2]};
   const T* ste = st + (int64_t)e * kStateFields * Q3;
   T gmu = T(0), glam = T(0);
@@ -97,7 +97,7 @@ vjp_kernel(const __grid_constant__ ElemParams<double, P> prm, const double* __re
     for (int c = 0; c < 3; ++c) sm[c * FQ + so] = T(0);
   }
   __syncthreads();
-  transpose_stages<T, P, true>(prm.tab, prm.pairs, sm);
+  transpose_stages<T, P, true>(prm.tab, prm.pairs, sm, threadIdx.x);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
     int so;

@@ -376,14 +376,13 @@ constexpr int elem_smem_words() {
 // All contractions use the even-odd half tables; `pairs` selects the nodal
 // pairing of the mode-side values.
 template <typename T, int P, bool GRAD>
-__device__ __forceinline__ void forward_stages(const ElemTables<T, P>& tb, int pairs, T* sm) {
+__device__ __forceinline__ void forward_stages(const ElemTables<T, P>& tb, int pairs, T* sm, int t) {
   using G = Geo<P>;
   constexpr int n = G::n, Q = G::Q, XQ = G::XQ, XN = G::XN, FQ = G::FQ;
   T* U = sm;
   T* R1 = sm + 3 * FQ;
   T* R2 = sm + 6 * FQ;
   T* R3 = sm + 9 * FQ;
-  const int t = threadIdx.x;
   {  // F1: lines (c, r, q)
     constexpr int L = n * n;
     if (t < 3 * L) {
@@ -452,14 +451,13 @@ __device__ __forceinline__ void forward_stages(const ElemTables<T, P>& tb, int p
 //   T2        y: A2' -> A1' [3][n][n][Q] (region 2)
 //   T1        x: A1' -> Y (region 1)
 template <typename T, int P, bool GRAD>
-__device__ __forceinline__ void transpose_stages(const ElemTables<T, P>& tb, int pairs, T* sm) {
+__device__ __forceinline__ void transpose_stages(const ElemTables<T, P>& tb, int pairs, T* sm, int t) {
   using G = Geo<P>;
   constexpr int n = G::n, Q = G::Q, XQ = G::XQ, XN = G::XN, FQ = G::FQ;
   T* U = sm;
   T* R1 = sm + 3 * FQ;
   T* R2 = sm + 6 * FQ;
   T* R3 = sm + 9 * FQ;
-  const int t = threadIdx.x;
   if (GRAD) {
     constexpr int L = Q * Q;
     if (t < 3 * L) {  // DTx: x-lines at (c, qz, qy)
@@ -581,7 +579,7 @@ __device__ __forceinline__ void residual_body(const ElemTables<double, P>& tb, i
     X[so] = u[g];
   }
   __syncthreads();
-  forward_stages<T, P, true>(tb, pairs, sm);
+  forward_stages<T, P, true>(tb, pairs, sm, threadIdx.x);
   const T sc[3] = {m.s[0], m.s[1], m.s[2]};
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
@@ -630,7 +628,7 @@ __device__ __forceinline__ void residual_body(const ElemTables<double, P>& tb, i
     for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= mfac;
   }
   __syncthreads();
-  transpose_stages<T, P, true>(tb, pairs, sm);
+  transpose_stages<T, P, true>(tb, pairs, sm, threadIdx.x);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
     int so;
@@ -671,9 +669,11 @@ constexpr int tangent_min_blocks() {
 // The tangent action on the element coefficients held in X (the gather's
 // shared layout): forward stages, pointwise linearised stress (and the fused
 // mass term), transposed stages; the result replaces X.
+// t: the thread's index within the element's G::NT threads (threadIdx.x
+// when a CTA serves one element).
 template <int P, typename T, bool STIFF>
 __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int pairs, const MeshParams<T>& m,
-                                               int e, const T* __restrict__ st, T* sm) {
+                                               int e, const T* __restrict__ st, T* sm, int t) {
   using G = Geo<P>;
   // float32: returns this thread's share of x_e . (K_e x_e).  The
   // transposed stages are the exact adjoint of the forward ones, so the
@@ -685,11 +685,11 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
   double dotq = 0.0;
   constexpr int Q = P + 2, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
   constexpr int NT = G::NT;
-  forward_stages<T, P, STIFF>(tb, pairs, sm);
+  forward_stages<T, P, STIFF>(tb, pairs, sm, t);
   const T sc[3] = {m.s[0], m.s[1], m.s[2]};
   const T* ste = st + (int64_t)e * kStateFields * Q3;
   if constexpr (!STIFF) {
-    for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
+    for (int q = t; q < Q3; q += NT) {
       const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
       const int so = (qz * Q + qy) * XQ + qx;
       const T mfac = m.b1 * m.rho * tb.W[qx] * tb.W[qy] * tb.W[qz] * m.detJ;
@@ -710,7 +710,7 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
     const T mus2[3] = {m.mu * m.detJ * sc[0] * sc[0], m.mu * m.detJ * sc[1] * sc[1],
                        m.mu * m.detJ * sc[2] * sc[2]};
     const T b1rho = m.b1 * m.rho * m.detJ;
-    for (int q = threadIdx.x; q < Q3; q += NT) {
+    for (int q = t; q < Q3; q += NT) {
       const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
       const int so = (qz * Q + qy) * XQ + qx;
       T H[3][3], Gr[3][3];
@@ -757,7 +757,7 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
       if (QDOT) dotq += (double)(qf + mfac * mq);
     }
   }
-  for (int q = threadIdx.x; STIFF && sizeof(T) == 8 && q < Q3; q += NT) {
+  for (int q = t; STIFF && sizeof(T) == 8 && q < Q3; q += NT) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
     const int so = (qz * Q + qy) * XQ + qx;
     T H[3][3], dF[3][3];
@@ -803,7 +803,7 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
     if (QDOT) dotq += (double)(wdet * qf + mfac * mq);
   }
   __syncthreads();
-  transpose_stages<T, P, STIFF>(tb, pairs, sm);
+  transpose_stages<T, P, STIFF>(tb, pairs, sm, t);
   return dotq;
 }
 
@@ -850,7 +850,7 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
   }
   __syncthreads();
   if (stat0 != 0) return;
-  double dotT = tangent_core<P, T, STIFF>(tb, pairs, m, e, st, sm);
+  double dotT = tangent_core<P, T, STIFF>(tb, pairs, m, e, st, sm, threadIdx.x);
   constexpr bool RELOAD = sizeof(T) == 8;  // float64: x_e . y_e from a second read of x
   if (fast) {
     const TV* xb = x + view.base;
@@ -921,7 +921,7 @@ __device__ __forceinline__ void mass_body(const ElemTables<T, P>& tb, int pairs,
     X[so] = (T)x[g];
   }
   __syncthreads();
-  forward_stages<T, P, false>(tb, pairs, sm);
+  forward_stages<T, P, false>(tb, pairs, sm, threadIdx.x);
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
     const int so = (qz * Q + qy) * XQ + qx;
@@ -930,7 +930,7 @@ __device__ __forceinline__ void mass_body(const ElemTables<T, P>& tb, int pairs,
     for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= f;
   }
   __syncthreads();
-  transpose_stages<T, P, false>(tb, pairs, sm);
+  transpose_stages<T, P, false>(tb, pairs, sm, threadIdx.x);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
     int so;
@@ -1117,7 +1117,7 @@ energy_kernel(const __grid_constant__ ElemParams<double, P> prm, const double* _
     X[so] = u[g];
   }
   __syncthreads();
-  forward_stages<T, P, true>(prm.tab, prm.pairs, sm);
+  forward_stages<T, P, true>(prm.tab, prm.pairs, sm, threadIdx.x);
   const T sc[3] = {prm.s[0], prm.s[1], prm.s[2]};
   T acc = T(0);
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
@@ -1178,7 +1178,7 @@ body_load_kernel(const __grid_constant__ ElemParams<double, P> prm, const double
     for (int c = 0; c < 3; ++c) sm[c * FQ + so] = wdet * fe[c * Q3 + q];
   }
   __syncthreads();
-  transpose_stages<T, P, false>(prm.tab, prm.pairs, sm);
+  transpose_stages<T, P, false>(prm.tab, prm.pairs, sm, threadIdx.x);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
     bool cons;
     int so;

@@ -64,6 +64,42 @@ template <int P>
 cudaError_t launch_batch_mass(const HostElemData& tabs, const HostBatchLaunch& L, int grid, const double* x,
                               double* y, cudaStream_t s);
 
+// Cross-order persistent launch of the batched tangent (batch_persist.cuh).
+// An item is up to kper[P] consecutive elements e0 .. e0 + count - 1 of the
+// problem with index `prob` in the per-problem table, of order P.
+struct PersistItem {
+  int P, prob, e0, count;
+};
+
+struct HostPersist {
+  const HostElemData* tabs[9] = {};   // the 1D tables of each order present (else null)
+  int kper[9] = {};                   // elements per item for each order
+};
+
+// One problem of the per-problem table (built on the host, uploaded as is).
+struct HostPersistProb {
+  HostMesh mesh;
+  int64_t dof_off = 0, st_off = 0, part_off = 0;
+  int pid = 0, nelem = 0;
+};
+
+// Bytes of one device-side table entry, and the host image of the table
+// (b1 is the mass coefficient of the operator).
+template <typename T>
+size_t persist_prob_bytes();
+template <typename T>
+void persist_probs_image(const std::vector<HostPersistProb>& probs, double b1, std::vector<unsigned char>& out);
+// Dynamic shared memory of the launch and its resident CTAs per SM (0 on error).
+template <typename T>
+size_t persist_smem(const HostPersist& hp);
+template <typename T, typename TV>
+int persist_occupancy(const HostPersist& hp);
+template <typename T, typename TV>
+cudaError_t launch_batch_persistent(const HostPersist& hp, int grid, const PersistItem* items, const int* nitems,
+                                    int* queue, const void* probs, const TV* x, TV* y, const T* st,
+                                    double* partial, PcgScalars* scal, cudaStream_t s);
+constexpr int kPersistMaxTile = 4;    // elements per item considered by the tuner
+
 template <int P>
 cudaError_t launch_cond_columns(const HostElemData& h, double b1, const double* st, double* Ke, cudaStream_t s);
 

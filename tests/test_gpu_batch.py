@@ -109,10 +109,19 @@ def test_batch_tangent_mixed():
         assert _rel(yh[seg], d.effective_apply(u[seg], x[seg], b1=10.0)) < TOL32, i
 
 
+# largest tile (elements per work item of the persistent launch) per order:
+# min(4, 320 // threads per element)
+MAX_TILE = {1: 4, 2: 4, 3: 3, 4: 2, 5: 2, 6: 1, 7: 1, 8: 1}
+
+
+@pytest.mark.parametrize("persist", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_batch_newmark_steps(prec):
+def test_batch_newmark_steps(prec, persist):
+    # persist = 1: the PCG operator as one launch across the order groups,
+    # each order at its largest tile (several elements per CTA)
     probs = _problems(seed=2, n=5, orders=(2, 3, 4), max_e=2)
     b = _batch(probs, "sdme_h", prec=prec)
+    b.set_persistent(persist, MAX_TILE if persist else None)
     ds = _oracles(probs, "sdme_h")
     mags = [0.05 * pr["mu"] for pr in probs]
     f = b.zeros()
@@ -141,6 +150,44 @@ def test_batch_newmark_steps(prec):
     assert len(stats) == b.nprob and all(st["newton_iters"] >= 1 for st in stats)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_persistent_high_orders(prec):
+    # orders 1, 5 and 8 in one persistent launch (P = 8 fills the CTA, P = 1
+    # and 5 share it among 4 and 2 elements), a ragged element count per
+    # problem (items end short), against the oracle's Newmark step
+    probs = [dict(elems=(2, 1, 1), lengths=(1.0, 0.7, 0.9), clamp={"zmin": (0, 1, 2)}, mu=400.0, lam=600.0,
+                  rho=1.0, P=8),
+             dict(elems=(3, 1, 2), lengths=(1.0, 0.8, 1.2), clamp={"zmin": (0, 1, 2)}, mu=900.0, lam=1500.0,
+                  rho=1.0, P=1),
+             dict(elems=(1, 3, 1), lengths=(0.9, 1.0, 0.8), clamp={"zmin": (0, 1, 2)}, mu=300.0, lam=900.0,
+                  rho=1.0, P=5)]
+    b = _batch(probs, "sdme_h", prec=prec)
+    b.set_persistent(1, MAX_TILE)
+    ds = _oracles(probs, "sdme_h")
+    f = b.zeros()
+    b.traction_load("zmax", [(0.0, 0.0, -0.05 * pr["mu"]) for pr in probs], f)
+    fh = _host(f)
+    u, v, a = b.zeros(), b.zeros(), b.zeros()
+    stats = b.newmark_step(u, v, a, 0.01, f, newton_tol=1e-12, pcg_rtol=1e-13, mixed_rtol=1e-5)
+    assert all(st["converged"] for st in stats)
+    assert b.persistent_info()["on"]
+    uh = _host(u)
+    z = [np.zeros(d.mesh.ndof) for d in ds]
+    for i, d in enumerate(ds):
+        seg = slice(b.offsets[i], b.offsets[i] + b.ndofs[i])
+        uo, _, _, _ = solvers.newmark_step(d, z[i], z[i], z[i], fh[seg], 0.01, tol=1e-12, linear="direct")
+        assert _rel(uh[seg], uo) < (1e-9 if prec == 0 else 1e-8), i
+
+
+def test_batch_persistent_tiles_validated():
+    import paper_2104_13466_gb300 as s
+    b = _batch(_problems(n=2), "sdme_h")
+    with pytest.raises(s.SdmeError):
+        b.set_persistent(1, {8: 2})          # a P = 8 element needs all 320 threads
+    with pytest.raises(s.SdmeError):
+        b.set_persistent(2)
+
+
 def test_batch_tuner_keeps_results():
     probs = _problems(seed=3, n=6)
     b = _batch(probs, "sdme_h")
@@ -152,6 +199,9 @@ def test_batch_tuner_keeps_results():
     tuned = b.tune(reps=2)
     assert sorted(p for p, _, _ in tuned) == sorted({pr["P"] for pr in probs})
     assert all(ms > 0 for _, _, ms in tuned)
+    info = b.persistent_info()
+    assert info["persist_ms"] > 0 and info["groups_ms"] > 0
+    assert all(1 <= info["kper"][pr["P"]] <= MAX_TILE[pr["P"]] for pr in probs)
     y1 = b.zeros()
     b.tangent_apply(_dev(u), 5.0, _dev(x), y1)
     assert _rel(_host(y1), _host(y0)) < 1e-13
