@@ -377,6 +377,12 @@ def compare_block(args, w, n_main, main_steps, saved, prec_main):
             cube["%s/%s" % (basis, pname)] = arm_summary(ctx.ndof, [ramp.step() for _ in range(wc["steps"])])
             ctx.close()
     out["cube_p4"] = cube
+    if args.compare_batch_steps > 0:
+        r = run_batch(args, workload("batch_cubes"), steps=args.compare_batch_steps, quiet=True, basis="sdme_h")
+        out["batch_cubes"] = {k: r[k] for k in ("problems", "total_dofs", "elements", "steps", "ms_per_step",
+                                                "matvec_dofs_per_s", "all_converged", "newton_iters_mean",
+                                                "pcg_iters_per_newton_mean", "pcg_iters_per_newton_max",
+                                                "persistent", "tuning")}
     return out
 
 
@@ -776,14 +782,16 @@ def compare_sequential(args, w, probs, b_full, f_full, dt, steps):
                       "max_rel_diff": diff}), flush=True)
 
 
-def run_batch(args, w):
+def run_batch(args, w, steps=None, persist=None, quiet=False, basis=None):
     """Batched independent solves (config 4 shape): 256 seeded cubes of uneven
     size, order and material, each taking `steps` implicit Newmark steps of a
     ramped top traction, all problems advanced together (one set of launches
     per step, PCG chunks replayed as one CUDA graph for the whole batch), in
     mixed precision (float32 tangent and PCG inside the float64 Newton
     residual).  Reports the aggregate tangent-matvec DOF/s over the timed
-    steps, the wall time, and the tuner's launch configuration per order."""
+    steps, the wall time, the tuner's launch configuration per order and the
+    persistent cross-order operator's tiles and timing (persist: 1 / 0 / -1
+    forces it on, off, or lets the tuner decide)."""
     import torch
     import paper_2104_13466_gb300 as sd
     from synthetic import batch_draws, load_magnitude
@@ -794,15 +802,20 @@ def run_batch(args, w):
         probs.append(dict(elems=(side[i],) * 3, lengths=(1.0, 1.0, 1.0), clamp=w["clamp"], mu=mu, lam=lam,
                           rho=w["rho"], P=orders[i]))
     prec = sd.MIXED_FP32 if args.precision == "mixed" else sd.FP64
+    basis = basis or args.basis
     t0 = time.time()
-    b = sd.Batch(probs, args.basis, precision=prec, k=w["k"], lam_h=w["lam"])
+    b = sd.Batch(probs, basis, precision=prec, k=w["k"], lam_h=w["lam"])
     t_create = time.time() - t0
+    persist = args.batch_persist if persist is None else persist
+    b.set_persistent(persist)
     smag = load_magnitude(w["load_key"])
     f = b.zeros()
     scale = (w["load_scale"] if args.batch_load_scale is None else args.batch_load_scale) * smag / 1.0e3
     b.traction_load(w["traction_face"], [(0.0, 0.0, -scale * E[i]) for i in range(w["count"])], f)
     tuning = b.tune(reps=3) if not args.no_tune else []
-    steps = args.batch_steps or w["steps"]
+    if persist != -1:
+        b.set_persistent(persist)   # keep the forced form (the tuner's tiles stay)
+    steps = steps or args.batch_steps or w["steps"]
     dt = w["dt"]
 
     def run(nsteps, time_it):
@@ -834,7 +847,7 @@ def run_batch(args, w):
     failed = sorted({i for st in stats for i in range(b.nprob) if not st[i]["converged"]})
     newton = [st[i]["newton_iters"] for st in stats for i in range(b.nprob)]
     pcg = [st[i]["pcg_iters_total"] / max(1, st[i]["newton_iters"]) for st in stats for i in range(b.nprob)]
-    out = {"mode": "batch", "workload": args.workload, "basis": args.basis, "precision": args.precision,
+    out = {"mode": "batch", "workload": "batch_cubes", "basis": basis, "precision": args.precision,
            "problems": b.nprob, "total_dofs": int(sum(b.ndofs)), "elements": int(sum(s_ ** 3 for s_ in side)),
            "steps": steps, "dt": dt, "wall_ms": ms, "ms_per_step": ms / steps,
            "matvec_dofs_per_s": dof_matvecs / (ms * 1e-3), "all_converged": conv,
@@ -845,7 +858,9 @@ def run_batch(args, w):
            "tuning": [{"P": p_, "grid": g_, "tangent_ms": m_} for p_, g_, m_ in tuning],
            "persistent": b.persistent_info()}
     b.close()
-    print(json.dumps(out), flush=True)
+    if not quiet:
+        print(json.dumps(out), flush=True)
+    return out
 
 
 def main():
@@ -886,6 +901,11 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--batch-load-scale", type=float, default=None)
     ap.add_argument("--batch-vs-sequential", type=int, default=0)
+    ap.add_argument("--batch-persist", type=int, default=-1, choices=[-1, 0, 1],
+                    help="batched PCG operator: 1 one persistent launch across orders, 0 one launch per order, "
+                         "-1 as the tuner decides")
+    ap.add_argument("--compare-batch-steps", type=int, default=3,
+                    help="steps of the 256-cube batch in the comparison block (0: skip)")
     args = ap.parse_args()
     if args.batch and args.workload == "beam_p8":
         args.workload = "batch_cubes"
