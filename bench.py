@@ -220,6 +220,56 @@ def cpu_oracle_matvec(w, basis, nsample, seed=0):
     return dofs_per_s, dt, os.cpu_count()
 
 
+def cpu_oracle_extras(w, basis, nsample):
+    """The other timings the CPU-baseline plan names, on the oracle as it
+    stands: config 1 (the 4^3-hex unit cube at P = 4) in full, 10 implicit
+    Newmark steps with Jacobi-PCG (rtol 1e-10, Newton 1e-8) in SDME-H; and
+    one internal-force evaluation on the cantilever's sample of elements,
+    scaled to the mesh (a Newton step of the 6.5 M-DOF cantilever would take
+    the oracle hours)."""
+    from oracle import solvers
+    from oracle.assembly import Discretization
+    from oracle.basis1d import Basis1D
+    from oracle.hexmesh import BoxMesh
+    from oracle.material import lame as olame
+    from synthetic import random_vector
+    out = {}
+    wc = workload("cube_p4")
+    mu, lam = olame(wc["E"], wc["nu"])
+    mesh = BoxMesh(*wc["elems"], wc["P"], wc["lengths"])
+    for f, comps in wc["clamp"].items():
+        mesh.clamp(f, comps)
+    d = Discretization(mesh, Basis1D(wc["P"], "sdme_h"), mu, lam, wc["rho"])
+    unit = d.traction_load(wc["traction_face"], lambda X, t: np.broadcast_to(wc["traction_dir"], X.shape))
+    smag = load_magnitude(wc["load_key"])
+    u = np.zeros(mesh.ndof)
+    v, a = u.copy(), u.copy()
+    t0 = time.perf_counter()
+    newton = 0
+    for k in range(1, wc["steps"] + 1):
+        u, v, a, st = solvers.newmark_step(d, u, v, a, unit * smag * k / wc["steps"], wc["dt"],
+                                           tol=wc["newton_tol"], pcg_rtol=wc["pcg_rtol"])
+        newton += len(st["pcg_iters"])
+    dt = time.perf_counter() - t0
+    out["cube_p4_newmark"] = {"ms_per_step": dt * 1e3 / wc["steps"], "steps": wc["steps"],
+                              "newton_iters_per_step": newton / wc["steps"], "basis": "sdme_h"}
+    mu, lam = olame(w["E"], w["nu"])
+    mesh = BoxMesh(*w["elems"], w["P"], w["lengths"])
+    for f, comps in w["clamp"].items():
+        mesh.clamp(f, comps)
+    d = Discretization(mesh, Basis1D(w["P"], basis), mu, lam, w["rho"])
+    uu = random_vector(mesh.ndof, 11, 1e-4)
+    els = np.arange(min(nsample, mesh.nelem))
+    t0 = time.perf_counter()
+    for s0 in range(0, len(els), 64):
+        e = els[s0:s0 + 64]
+        d.scatter(d.ref.internal_force(d.gather(uu, e), mu, lam), e)
+    dt = time.perf_counter() - t0
+    out["beam_internal_force"] = {"dofs_per_s": mesh.ndof * (len(els) / mesh.nelem) / dt,
+                                  "sample": "%d of %d elements, scaled to the mesh" % (len(els), mesh.nelem)}
+    return out
+
+
 def workload_config(args, w, ws):
     """The `config` object of the default line, identical for both arms."""
     ne, P = w["elems"], w["P"]
@@ -397,6 +447,7 @@ def run_gpu(args, w):
         dist.init_process_group("nccl")
     prec = sd.MIXED_FP32 if args.precision == "mixed" else sd.FP64
     ctx = make_context(sd, w, args.basis, prec)
+    tangent_grid = ctx.set_tangent_grid(args.tangent_grid)
     n = ctx.ndof
     dev = torch.device("cuda", local)
     opts = newton_opts(args, w)
@@ -481,6 +532,8 @@ def run_gpu(args, w):
         cpu = {"value": cv, "unit": "DOF/s", "cores": cores, "kind": "oracle",
                "sample": "FP64 numpy oracle tangent action on %d of %d elements (%.1f s), scaled to the mesh"
                          % (args.ref_sample, int(np.prod(w["elems"])), cdt)}
+        if args.cpu_extras:
+            cpu["extra"] = cpu_oracle_extras(w, args.basis, args.ref_sample)
     clocks = clk.summary()
     compare = None
     if rank == 0 and not args.no_compare:
@@ -500,7 +553,7 @@ def run_gpu(args, w):
                          "traffic": profiled_traffic(args.precision) if w["P"] == 8 and args.workload == "beam_p8"
                          else None,
                          "kernel": "tangent_kernel<8,%s>" % ("float,float" if prec == sd.MIXED_FP32 else "double,double"),
-                         "avg_launch_ms": avg_tan, "launches": tan_launches,
+                         "avg_launch_ms": avg_tan, "launches": tan_launches, "tangent_grid": tangent_grid,
                          "flops_per_launch": flops, "flops_unit": "plain sum factorisation, 859,680 per P=8 element",
                          "flops_per_launch_even_odd": flops_impl,
                          "peak_src": "derived from recipe unit counts and max clock",
@@ -535,6 +588,7 @@ def run_kernel_only(args, w):
     u = torch.from_numpy(random_vector(n, 1, 1e-4)).cuda()
     b = torch.from_numpy(random_vector(n, 2)).cuda()
     x = torch.zeros_like(u)
+    grid = ctx.set_tangent_grid(args.tangent_grid)
     ctx.set_timing(True)
     its, rel = ctx.pcg_solve(u, 4.0, b, x, rtol=0.0, maxit=args.kernel_iters, allow_maxit=True)
     t = ctx.timing()
@@ -542,6 +596,7 @@ def run_kernel_only(args, w):
     flops = algorithmic_flops_per_element(w["P"]) * ctx.nelem
     flops_eo = tangent_flops_per_element(w["P"], args.basis == "nodal") * ctx.nelem
     print(json.dumps({"mode": "kernel-only", "precision": args.precision, "basis": args.basis, "iters": its,
+                      "tangent_grid": grid,
                       "tangent_avg_ms": avg, "tflops": flops / (avg * 1e-3) / 1e12,
                       "tflops_even_odd_count": flops_eo / (avg * 1e-3) / 1e12, "launches": t["tangent_launches"]}),
           flush=True)
@@ -880,6 +935,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--ref-sample", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-extras", action="store_true",
+                    help="also time the oracle on config 1 in full and a sampled internal force (minutes of CPU)")
     ap.add_argument("--kernel-only", action="store_true")
     ap.add_argument("--compare", action="store_true")
     ap.add_argument("--explicit", action="store_true")
@@ -893,6 +950,8 @@ def main():
     ap.add_argument("--compare-levels", type=int, default=5)
     ap.add_argument("--precisions", default="mixed,fp64")
     ap.add_argument("--kernel-iters", type=int, default=20)
+    ap.add_argument("--tangent-grid", type=int, default=0,
+                    help="CTAs of the PCG tangent launch: 0 one per element, -1 the resident CTAs, > 0 that many")
     ap.add_argument("--adjoint", action="store_true")
     ap.add_argument("--forcing", type=int, default=1, choices=[0, 1],
                     help="1: Eisenstat-Walker forcing terms for the inner PCG tolerance (0: fixed tolerance)")

@@ -439,10 +439,24 @@ sdme_status sdme_get_timing(sdme_ctx* ctx, sdme_timing* out);
  * MIXED_FP32 contexts: the largest number of float64-residual restarts
  * (iterative refinement) of one float32 PCG solve; 0 turns the refinement
  * off (the float32 recurrence's own test ends the solve).  Default 8.
- * Applies to the tangent and mass solves; ignored by FP64 contexts.
+ * Applies to the tangent solves (Newton steps, sdme_pcg_solve); mass solves
+ * (explicit steps, sdme_mass_solve) end on the float32 recurrence's test.
+ * Ignored by FP64 contexts.
  * SDME_EINVAL for a negative count.
  */
 sdme_status sdme_set_refinement(sdme_ctx* ctx, int max_restarts);
+
+/*
+ * Launch shape of the tangent operator inside PCG (hexahedral meshes):
+ * ctas = 0 one CTA per element (the default); ctas = -1 as many CTAs as fit
+ * on the GPU at once (resident CTAs per SM x SMs); ctas > 0 that many.  With
+ * a fixed grid each CTA serves elements blockIdx, blockIdx + grid, ..., and
+ * sums its share of p.(A p) over them in that order (results stay
+ * deterministic).  Drops the captured PCG graph.  SDME_EINVAL for ctas < -1.
+ * sdme_get_tangent_grid returns the grid in use (0: one CTA per element).
+ */
+sdme_status sdme_set_tangent_grid(sdme_ctx* ctx, int ctas);
+int sdme_get_tangent_grid(const sdme_ctx* ctx);
 
 /*
  * y_dev = (b1 M + K_T(u)) x_dev in float64, like sdme_tangent_apply, but
@@ -564,7 +578,8 @@ sdme_status sdme_batch_tune(sdme_batch* b, int reps, int ngroups_max, int* ngrou
  * of threads per element) from a device counter until none is left; each
  * problem's last element to finish sums the problem's step-length partials.
  * No CTA waits on another.  mode: 1 always, 0 never (one launch per order
- * group), -1 (the default) as sdme_batch_tune decides.  kper (host, 9
+ * group), -1 (the default) as sdme_batch_tune decides, and then only while
+ * problems of at least two orders are running.  kper (host, 9
  * entries indexed by P, may be NULL to keep the current ones): elements per
  * work item for each order, 1 up to min(4, 320 / threads per element)
  * (threads per element: 3 (P+2)^2 rounded up to a multiple of 32), else
@@ -574,13 +589,16 @@ sdme_status sdme_batch_tune(sdme_batch* b, int reps, int ngroups_max, int* ngrou
 sdme_status sdme_batch_set_persistent(sdme_batch* b, int mode, const int* kper);
 
 /*
- * The persistent form's state: *on (1 when the PCG iterations use it),
- * kper[9] (elements per work item by order, index = P), the tuner's time
- * of one persistent launch over the whole batch and the sum of the
- * per-order launch times (ms, -1 before tuning).  Any pointer may be NULL.
+ * The persistent form's state: *on (1 when the PCG iterations may use it;
+ * with mode -1 they do while at least two orders have running problems,
+ * one order running being that order's single launch), kper[9] (elements
+ * per work item by order, index = P), the tuner's time of one persistent
+ * launch over the whole batch, the sum of the per-order launch times and
+ * order_ms[9] (the persistent launch over one order's problems at its
+ * chosen tile) (ms, -1 before tuning).  Any pointer may be NULL.
  */
 sdme_status sdme_batch_persistent_info(const sdme_batch* b, int* on, int kper[9], float* persist_ms,
-                                       float* groups_ms);
+                                       float* groups_ms, float order_ms[9]);
 
 /* Kernel launches issued by the batch so far (all kinds). */
 sdme_status sdme_batch_launches(const sdme_batch* b, int64_t* launches);

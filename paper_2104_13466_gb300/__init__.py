@@ -38,7 +38,7 @@ EXPORTS = ("sdme_status_string", "sdme_build_basis1d", "sdme_create", "sdme_dest
            "sdme_batch_layout", "sdme_batch_internal_force", "sdme_batch_tangent_apply", "sdme_batch_traction_load",
            "sdme_batch_newmark_step", "sdme_batch_tune", "sdme_batch_launches", "sdme_static_solve",
            "sdme_set_condensation", "sdme_set_refinement", "sdme_gauss_point_coords", "sdme_batch_set_persistent",
-           "sdme_batch_persistent_info")
+           "sdme_batch_persistent_info", "sdme_set_tangent_grid", "sdme_get_tangent_grid")
 
 
 class BasisDesc(ctypes.Structure):
@@ -142,8 +142,10 @@ def _load():
     lib.sdme_set_refinement.argtypes = [vp, i]
     lib.sdme_gauss_point_coords.argtypes = [vp, vp]
     lib.sdme_batch_set_persistent.argtypes = [vp, i, ctypes.POINTER(i)]
+    lib.sdme_set_tangent_grid.argtypes = [vp, i]
+    lib.sdme_get_tangent_grid.argtypes = [vp]
     lib.sdme_batch_persistent_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_float),
-                                               ctypes.POINTER(ctypes.c_float)]
+                                               ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
     lib.sdme_get_timing.argtypes = [vp, ctypes.POINTER(Timing)]
     lib.sdme_tangent_apply_noalloc.argtypes = [ctypes.POINTER(MeshDesc), ctypes.POINTER(Material), i, pd, pd, pd,
                                                pd, vp, d, vp, vp, vp]
@@ -428,6 +430,12 @@ class Context:
     def set_timing(self, enable=True):
         return _check(lib.sdme_set_timing(self._h, int(bool(enable))), "sdme_set_timing")
 
+    def set_tangent_grid(self, ctas):
+        """CTAs of the PCG tangent launch: 0 one per element, -1 the resident
+        CTAs, > 0 that many (sdme_set_tangent_grid); returns the grid in use."""
+        _check(lib.sdme_set_tangent_grid(self._h, int(ctas)), "sdme_set_tangent_grid", ctx=self._h)
+        return lib.sdme_get_tangent_grid(self._h)
+
     def set_refinement(self, max_restarts):
         """Float64-residual restarts allowed per float32 PCG solve (0: off)."""
         return _check(lib.sdme_set_refinement(self._h, int(max_restarts)), "sdme_set_refinement")
@@ -679,7 +687,8 @@ class Batch:
         on = ctypes.c_int()
         kper = (ctypes.c_int * 9)()
         pm, gm = ctypes.c_float(), ctypes.c_float()
-        _check(lib.sdme_batch_persistent_info(self._h, ctypes.byref(on), kper, ctypes.byref(pm), ctypes.byref(gm)),
-               "sdme_batch_persistent_info")
+        om = (ctypes.c_float * 9)()
+        _check(lib.sdme_batch_persistent_info(self._h, ctypes.byref(on), kper, ctypes.byref(pm), ctypes.byref(gm),
+                                              om), "sdme_batch_persistent_info")
         return {"on": bool(on.value), "kper": {P: kper[P] for P in range(1, 9)}, "persist_ms": pm.value,
-                "groups_ms": gm.value}
+                "groups_ms": gm.value, "order_ms": {P: om[P] for P in range(1, 9) if om[P] >= 0}}

@@ -112,6 +112,9 @@ struct sdme_ctx {
   // restarts from the float64 residual per solve (0: off), and the outcome
   // of the last solve
   int refine_max = 8;
+  // CTAs of the PCG's tangent launch: 0 one per element, else that many
+  // CTAs serving every tan_grid-th element (sdme_set_tangent_grid)
+  int tan_grid = 0;
   int last_sweeps = 0;
   double last_true_rel = -1.0;
   // Newton work vectors
@@ -206,14 +209,14 @@ sdme_status sync_and_check(sdme_ctx* ctx) {
 
 template <typename T, typename TV>
 sdme_status tangent_launch(sdme_ctx* ctx, double b1, const TV* x, TV* y, double* partial, PcgScalars* scal,
-                           cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr, bool defer = false) {
+                           cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr, bool defer = false, int grid = 0) {
   const HostElemData& h = ctx->h;
   const T* st;
   if constexpr (sizeof(T) == 8) st = ctx->st64;
   else st = ctx->st32;
   if (e0) SDME_CUDA(cudaEventRecord(e0, ctx->stream));
   SDME_CUDA(dispatch_P(h.P, [&](auto Pc) {
-    return launch_tangent<decltype(Pc)::value, T, TV>(h, b1, x, y, st, partial, scal, ctx->stream, defer);
+    return launch_tangent<decltype(Pc)::value, T, TV>(h, b1, x, y, st, partial, scal, ctx->stream, defer, grid);
   }));
   if (e1) SDME_CUDA(cudaEventRecord(e1, ctx->stream));
   ctx->kernel_launches += 1;
@@ -253,9 +256,13 @@ enum PcgOp { kOpTangent = 0, kOpMass = 1, kOpCondensed = 2 };
 // Issue one chunk of PCG iterations (operator, update, direction) on ctx->stream.
 template <typename T, typename TV>
 sdme_status pcg_chunk(sdme_ctx* ctx, double b1, int op, bool tim, TV* r, TV* p, TV* q, TV* dinv, TV* xh, TV* xl) {
-  // hexahedral tangent / mass operators leave p.(A p) as per-element
-  // partials for the update kernel (no last-CTA finalize in the operator)
-  const bool defer = op != kOpCondensed && ctx->h.dim == 3 && ctx->h.nelem <= kDeferMaxElems;
+  // hexahedral tangent / mass operators leave p.(A p) as per-element (or,
+  // with a fixed tangent grid, per-CTA) partials for the update kernel (no
+  // last-CTA finalize in the operator)
+  const int tgrid = (op == kOpTangent && ctx->h.dim == 3 && ctx->tan_grid > 0 && ctx->tan_grid < ctx->h.nelem)
+                        ? ctx->tan_grid : 0;
+  const int nparts = tgrid ? tgrid : (int)ctx->h.nelem;
+  const bool defer = op != kOpCondensed && ctx->h.dim == 3 && nparts <= kDeferMaxElems;
   for (int j = 0; j < kPcgChunk; ++j) {
     if (op == kOpCondensed) {
       if constexpr (sizeof(TV) == 8) {
@@ -275,12 +282,11 @@ sdme_status pcg_chunk(sdme_ctx* ctx, double b1, int op, bool tim, TV* r, TV* p, 
       ctx->kernel_launches += 1;
     } else {
       SDME_TRY((tangent_launch<T, TV>(ctx, b1, p, q, ctx->partial, ctx->scal, tim ? ctx->ev[2 * j] : nullptr,
-                                      tim ? ctx->ev[2 * j + 1] : nullptr, defer)));
+                                      tim ? ctx->ev[2 * j + 1] : nullptr, defer, tgrid)));
     }
     constexpr int vi = sizeof(TV) == 4 ? 1 : 0;
     k_pcg_update<TV><<<ctx->upd_blocks[vi], kVecThreads, 0, ctx->stream>>>(
-        ctx->ndof, r, q, dinv, ctx->scal, ctx->partial + ctx->upart_off, defer ? ctx->partial : nullptr,
-        (int)ctx->h.nelem);
+        ctx->ndof, r, q, dinv, ctx->scal, ctx->partial + ctx->upart_off, defer ? ctx->partial : nullptr, nparts);
     k_pcg_direction<TV><<<ctx->dir_blocks[vi], kVecThreads, 0, ctx->stream>>>(ctx->ndof, r, dinv, p, xh, xl,
                                                                              ctx->scal);
   }
@@ -364,7 +370,9 @@ sdme_status pcg_core(sdme_ctx* ctx, double b1, int op, const double* b, double* 
                                                               ctx->partial, rtol, maxit);
   SDME_CUDA(cudaGetLastError());
   ctx->kernel_launches += 1;
-  const bool refine = sizeof(TV) == 4 && ctx->refine_max > 0 && (op == kOpTangent || op == kOpMass);
+  // mass solves are not refined: the consistent mass is well conditioned and
+  // the explicit scheme's mixed tolerance (1e-6) is within float32 reach
+  const bool refine = sizeof(TV) == 4 && ctx->refine_max > 0 && op == kOpTangent;
   int done_iters = 0, sweeps = 0;
   double true_rel = -1.0;
   for (;;) {
@@ -1407,6 +1415,32 @@ const char* sdme_cuda_error_string(const sdme_ctx* ctx) {
   if (!ctx) return "no context";
   return cudaGetErrorString(ctx->last_cuda != cudaSuccess ? ctx->last_cuda : ctx->last_timing_error);
 }
+
+sdme_status sdme_set_tangent_grid(sdme_ctx* ctx, int ctas) {
+  if (!ctx || ctas < -1) return SDME_EINVAL;
+  int grid = ctas;
+  if (ctas == -1) {
+    int per_sm = 0, dev = 0, sms = 0;
+    SDME_CUDA(dispatch_P(ctx->h.P, [&](auto Pc) {
+      constexpr int P = decltype(Pc)::value;
+      per_sm = ctx->prec == SDME_MIXED_FP32 ? tangent_resident_ctas<P, float, float>()
+                                             : tangent_resident_ctas<P, double, double>();
+      return cudaSuccess;
+    }));
+    SDME_CUDA(cudaGetDevice(&dev));
+    SDME_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (per_sm < 1) return SDME_ECUDA;
+    grid = per_sm * sms;
+  }
+  ctx->tan_grid = grid;
+  if (ctx->gexec[0]) {  // the captured PCG chunk holds the old launch shape
+    cudaGraphExecDestroy(ctx->gexec[0]);
+    ctx->gexec[0] = nullptr;
+  }
+  return SDME_OK;
+}
+
+int sdme_get_tangent_grid(const sdme_ctx* ctx) { return ctx ? ctx->tan_grid : -1; }
 
 sdme_status sdme_set_refinement(sdme_ctx* ctx, int max_restarts) {
   if (!ctx || max_restarts < 0) return SDME_EINVAL;

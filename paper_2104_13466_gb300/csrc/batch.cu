@@ -113,9 +113,13 @@ struct sdme_batch {
   // cross-order persistent PCG operator
   int persist_mode = -1;      // -1: the tuner decides, 0: per-order launches, 1: persistent
   bool persist_on = false;
+  bool persist_use = false;   // the current chunk graph uses the persistent launch (>= 2 running orders)
+  float persist_order_ms[9] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};   // tuner, per order
   int kper[9] = {0, 1, 1, 1, 1, 1, 1, 1, 1};
   float persist_ms = -1.f, groups_ms = -1.f;
-  int persist_grid = 0;
+  int persist_grid = 0;       // resident CTAs of the persistent launch
+  int persist_items_n = 0;    // work items uploaded (the launch needs no more CTAs than that)
+  int persist_run_orders[9] = {};   // orders among the uploaded items (they set the launch's shared memory)
   double persist_b1 = -1.0;   // b1 of the uploaded per-problem table
   PersistItem* items = nullptr;
   int* nitems = nullptr;
@@ -218,10 +222,13 @@ const T* b_state(sdme_batch* b) {
   else return b->st32;
 }
 
-// The persistent launch's view of the batch: each order's tables and tile.
+// The persistent launch's view of the batch: the tables and tile of each
+// order among the uploaded work items (the launch's shared memory and
+// resident CTAs follow from those orders only).
 HostPersist b_persist_desc(sdme_batch* b) {
   HostPersist hp;
   for (Group& g : b->groups) {
+    if (!b->persist_run_orders[g.P]) continue;
     hp.tabs[g.P] = &g.tabs;
     hp.kper[g.P] = b->kper[g.P];
   }
@@ -246,6 +253,10 @@ sdme_status b_persist_items(sdme_batch* b, const std::vector<int>* run, double b
       items.push_back(PersistItem{pr.P, i, (int)e, (int)std::min<int64_t>(K, pr.nelem - e)});
   }
   const int n = (int)items.size();
+  b->persist_items_n = n;
+  for (int P = 0; P <= 8; ++P) b->persist_run_orders[P] = 0;
+  for (const PersistItem& it : items) b->persist_run_orders[it.P] = 1;
+  B_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream));
   if (n > 0)
     B_CUDA(cudaMemcpyAsync(b->items, items.data(), sizeof(PersistItem) * n, cudaMemcpyHostToDevice, b->stream));
   B_CUDA(cudaMemcpyAsync(b->nitems, &n, sizeof(int), cudaMemcpyHostToDevice, b->stream));
@@ -271,11 +282,15 @@ sdme_status b_persist_items(sdme_batch* b, const std::vector<int>* run, double b
   return SDME_OK;
 }
 
+// reset_queue: clear the work counter first (else the preceding PCG update
+// kernel has cleared it, or the item upload did)
 template <typename T, typename TV>
-sdme_status b_persist_launch(sdme_batch* b, const TV* x, TV* y, double* partial, PcgScalars* scal) {
-  B_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream));
+sdme_status b_persist_launch(sdme_batch* b, const TV* x, TV* y, double* partial, PcgScalars* scal,
+                             bool reset_queue = false) {
+  if (reset_queue) B_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream));
   const HostPersist hp = b_persist_desc(b);
-  B_CUDA((launch_batch_persistent<T, TV>(hp, b->persist_grid, b->items, b->nitems, b->queue, b->pprobs, x, y,
+  const int grid = std::max(1, std::min(b->persist_grid, b->persist_items_n));
+  B_CUDA((launch_batch_persistent<T, TV>(hp, grid, b->items, b->nitems, b->queue, b->pprobs, x, y,
                                           b_state<T>(b), partial, scal, b->stream)));
   b->launches += 1;
   return SDME_OK;
@@ -389,10 +404,10 @@ struct BatchSideScope {
 template <typename T, typename TV>
 sdme_status b_pcg_chunk(sdme_batch* b, double b1, TV* r, TV* p, TV* q, TV* dinv, TV* xv) {
   for (int j = 0; j < kChunk; ++j) {
-    if (b->persist_on) B_TRY((b_persist_launch<T, TV>(b, p, q, b->partial, b->scal)));
+    if (b->persist_use) B_TRY((b_persist_launch<T, TV>(b, p, q, b->partial, b->scal)));
     else B_TRY((b_tangent<T, TV>(b, b1, p, q, b->partial, b->scal, true)));
     kb_pcg_update<TV><<<b->vec_grid, kVecThreads, 0, b->stream>>>(b->info, b->cta_prob, xv, r, p, q, dinv, b->scal,
-                                                                  b->partial);
+                                                                  b->partial, b->persist_use ? b->queue : nullptr);
     kb_pcg_direction<TV><<<b->vec_grid, kVecThreads, 0, b->stream>>>(b->info, b->cta_prob, r, dinv, p, b->scal);
     b->launches += 2;
   }
@@ -432,9 +447,18 @@ sdme_status b_pcg(sdme_batch* b, double b1, const double* rhs, double* x_out, do
         b->gexec = nullptr;
       }
       build_run_launches(b, run);
-      if (b->persist_on) {
-        if (!b->persist_grid) B_TRY(b_persist_grid(b));
+      // the persistent launch merges orders; with one order running the
+      // per-order launch is that order's single launch (and measured faster)
+      int orders_running = 0;
+      {
+        bool seen[9] = {};
+        for (int i : run) seen[b->probs[i].P] = true;
+        for (int P = 1; P <= 8; ++P) orders_running += seen[P] ? 1 : 0;
+      }
+      b->persist_use = b->persist_on && (orders_running >= 2 || b->persist_mode == 1);
+      if (b->persist_use) {
         B_TRY(b_persist_items(b, &run, b1));
+        B_TRY(b_persist_grid(b));
       }
       if (!b->warm) {  // the first chunk runs directly (sets the kernels' attributes)
         B_TRY((b_pcg_chunk<T, TV>(b, b1, r, p, q, dinv, xv)));
@@ -459,7 +483,7 @@ sdme_status b_pcg(sdme_batch* b, double b1, const double* rhs, double* x_out, do
     }
     B_CUDA(cudaGraphLaunch(b->gexec, b->stream));
     int64_t per = 2 * kChunk;
-    if (b->persist_on) per += kChunk;
+    if (b->persist_use) per += kChunk;
     else
       for (const Group& g : b->groups) per += kChunk * (int64_t)g.run_launches.size();
     b->launches = l0 + per;
@@ -881,8 +905,10 @@ sdme_status sdme_batch_set_persistent(sdme_batch* b, int mode, const int* kper) 
 }
 
 sdme_status sdme_batch_persistent_info(const sdme_batch* b, int* on, int kper[9], float* persist_ms,
-                                       float* groups_ms) {
+                                       float* groups_ms, float order_ms[9]) {
   if (!b) return SDME_EINVAL;
+  if (order_ms)
+    for (int P = 0; P <= 8; ++P) order_ms[P] = b->persist_order_ms[P];
   if (on) *on = b->persist_on ? 1 : 0;
   if (kper)
     for (int P = 0; P <= 8; ++P) kper[P] = b->kper[P];
@@ -963,8 +989,8 @@ sdme_status sdme_batch_tune(sdme_batch* b, int reps, int ngroups_max, int* ngrou
       float t = 0.f;
       for (int r = -1; r < reps; ++r) {
         if (r == 0) B_CUDA(cudaEventRecord(e0, b->stream));
-        B_TRY((mixed ? b_persist_launch<float, float>(b, b->p32, b->q32, b->partial, b->scal)
-                     : b_persist_launch<double, double>(b, b->p64, b->q64, b->partial, b->scal)));
+        B_TRY((mixed ? b_persist_launch<float, float>(b, b->p32, b->q32, b->partial, b->scal, true)
+                     : b_persist_launch<double, double>(b, b->p64, b->q64, b->partial, b->scal, true)));
       }
       B_CUDA(cudaEventRecord(e1, b->stream));
       B_CUDA(cudaEventSynchronize(e1));
@@ -980,8 +1006,8 @@ sdme_status sdme_batch_tune(sdme_batch* b, int reps, int ngroups_max, int* ngrou
       for (int k = 1; k <= kmax && result == SDME_OK; ++k) {
         b->kper[g.P] = k;
         float t = 0.f;
-        result = b_persist_grid(b);
-        if (result == SDME_OK) result = b_persist_items(b, nullptr, 0.0, g.P);
+        result = b_persist_items(b, nullptr, 0.0, g.P);
+        if (result == SDME_OK) result = b_persist_grid(b);
         if (result == SDME_OK) result = time_persist(&t);
         if (result == SDME_OK && (best < 0.f || t < best)) {
           best = t;
@@ -989,9 +1015,10 @@ sdme_status sdme_batch_tune(sdme_batch* b, int reps, int ngroups_max, int* ngrou
         }
       }
       b->kper[g.P] = bestk;
+      b->persist_order_ms[g.P] = best;
     }
-    if (result == SDME_OK) result = b_persist_grid(b);
     if (result == SDME_OK) result = b_persist_items(b, nullptr, 0.0);
+    if (result == SDME_OK) result = b_persist_grid(b);
     if (result == SDME_OK) result = time_persist(&b->persist_ms);
     b->persist_on = result == SDME_OK && (b->persist_mode == 1 || b->persist_ms < b->groups_ms);
     b->persist_b1 = -1.0;   // rebuilt with the solve's b1

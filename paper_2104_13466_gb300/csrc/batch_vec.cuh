@@ -170,7 +170,11 @@ __global__ void __launch_bounds__(kVecThreads) kb_pcg_update(const BatchVecInfo*
                                                              const int* __restrict__ cta_prob, TV* __restrict__ x,
                                                              TV* __restrict__ r, const TV* __restrict__ p,
                                                              TV* __restrict__ q, const TV* __restrict__ dinv,
-                                                             PcgScalars* scal, double* __restrict__ partial) {
+                                                             PcgScalars* scal, double* __restrict__ partial,
+                                                             int* __restrict__ queue = nullptr) {
+  // the persistent operator's work counter (if any) is free again: this
+  // launch follows the operator, the next operator follows the direction
+  if (queue && blockIdx.x == 0 && threadIdx.x == 0) *queue = 0;
   const BatchCta b(info, cta_prob);
   PcgScalars* sc = scal + b.p;
   if (sc->status != kPcgRunning) return;

@@ -812,7 +812,8 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
                                              const TV* __restrict__ x, TV* __restrict__ y,
                                              const T* __restrict__ st, double* __restrict__ dot_partial,
                                              unsigned nparts, PcgScalars* __restrict__ scal, T* sm,
-                                             const int* __restrict__ loc = nullptr, bool defer = false) {
+                                             const int* __restrict__ loc = nullptr, bool defer = false,
+                                             double* acc = nullptr) {
   using G = Geo<P>;
   constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q;
   constexpr int NT = G::NT;  // == blockDim.x: compile-time strides let the loops batch their loads
@@ -881,6 +882,10 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
     // and across CTAs in a fixed order: by the last CTA to finish here, or
     // (defer) by every CTA of the following PCG update.
     const double tot = block_sum(dotT);
+    if (acc) {  // a CTA serving several elements sums them (see tangent_kernel_strided)
+      if (threadIdx.x == 0) *acc += tot;
+      return;
+    }
     if (threadIdx.x == 0) dot_partial[e] = tot;
     if (scal && !defer && last_arrival(&scal->counter, nparts)) {
       const double pq = ordered_sum(dot_partial, (int)nparts);
@@ -902,6 +907,37 @@ tangent_kernel(const __grid_constant__ ElemParams<T, P> prm, const TV* __restric
   extern __shared__ __align__(16) unsigned char smem_raw[];
   tangent_body<P, T, TV, STIFF>(prm.tab, prm.pairs, prm, blockIdx.x, x, y, st, dot_partial, gridDim.x, scal,
                                 reinterpret_cast<T*>(smem_raw), prm.loc, defer != 0);
+}
+
+// The same operator with a fixed grid of CTAs (normally the resident ones)
+// each serving elements blockIdx.x, blockIdx.x + gridDim.x, ...: the CTA's
+// share of x . (K x) is summed over its elements in that order into
+// dot_partial[blockIdx.x], so the step length sums gridDim.x partials
+// instead of one per element, and no wave of CTAs ends part-empty.
+template <int P, typename T, typename TV>
+__global__ void __launch_bounds__(elem_threads(P), tangent_min_blocks<T>())
+tangent_kernel_strided(const __grid_constant__ ElemParams<T, P> prm, const TV* __restrict__ x,
+                       TV* __restrict__ y, const T* __restrict__ st, double* __restrict__ dot_partial,
+                       PcgScalars* __restrict__ scal, int defer, int nelem) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double acc = 0.0;   // thread 0's running sum
+  for (int e = blockIdx.x; e < nelem; e += gridDim.x) {
+    __syncthreads();  // the previous element's shared data has been consumed
+    tangent_body<P, T, TV, true>(prm.tab, prm.pairs, prm, e, x, y, st, dot_partial, gridDim.x, scal,
+                                 reinterpret_cast<T*>(smem_raw), prm.loc, defer != 0, dot_partial ? &acc : nullptr);
+  }
+  if (dot_partial) {
+    if (threadIdx.x == 0) dot_partial[blockIdx.x] = acc;
+    if (scal && !defer && last_arrival(&scal->counter, gridDim.x)) {
+      const double pq = ordered_sum(dot_partial, (int)gridDim.x);
+      if (threadIdx.x == 0) {
+        scal->pq = pq;
+        scal->alpha = scal->rz / pq;
+        if (!(pq > 0.0) || !isfinite(scal->alpha)) scal->status = kPcgBreakdown;
+        scal->counter = 0;
+      }
+    }
+  }
 }
 
 //-----------------------------------------------------------------------------

@@ -98,18 +98,34 @@ cudaError_t launch_residual(const HostElemData& h, double b1, const double* u, d
 
 template <int P, typename T, typename TV>
 cudaError_t launch_tangent(const HostElemData& h, double b1, const TV* x, TV* y, const T* st,
-                           double* partial, PcgScalars* scal, cudaStream_t s, bool defer) {
+                           double* partial, PcgScalars* scal, cudaStream_t s, bool defer, int grid) {
   if (h.dim == 2) return launch_quad_tangent<P, T, TV, true>(h, b1, x, y, st, partial, scal, s);
   static bool init = false;
   const size_t smem = sizeof(T) * elem_smem_words<P>();
   if (!init) {
     cudaError_t e = set_smem(tangent_kernel<P, T, TV>, smem);
+    if (e == cudaSuccess) e = set_smem(tangent_kernel_strided<P, T, TV>, smem);
     if (e != cudaSuccess) return e;
     init = true;
   }
   auto prm = make_params<T, P>(h, b1);
-  tangent_kernel<P, T, TV><<<h.nelem, elem_threads(P), smem, s>>>(prm, x, y, st, partial, scal, defer ? 1 : 0);
+  if (grid > 0 && grid < h.nelem)
+    tangent_kernel_strided<P, T, TV><<<grid, elem_threads(P), smem, s>>>(prm, x, y, st, partial, scal, defer ? 1 : 0,
+                                                                         h.nelem);
+  else
+    tangent_kernel<P, T, TV><<<h.nelem, elem_threads(P), smem, s>>>(prm, x, y, st, partial, scal, defer ? 1 : 0);
   return cudaGetLastError();
+}
+
+template <int P, typename T, typename TV>
+int tangent_resident_ctas() {
+  const size_t smem = sizeof(T) * elem_smem_words<P>();
+  if (set_smem(tangent_kernel_strided<P, T, TV>, smem) != cudaSuccess) return 0;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tangent_kernel_strided<P, T, TV>, elem_threads(P), smem) !=
+      cudaSuccess)
+    return 0;
+  return nb;
 }
 
 template <int P, typename T>
@@ -204,13 +220,15 @@ cudaError_t launch_body_load(const HostElemData& h, const double* fq, double* y,
                                           float*, int*, cudaStream_t);                                \
   template cudaError_t launch_tangent<P, double, double>(const HostElemData&, double, const double*,   \
                                                          double*, const double*, double*, PcgScalars*, \
-                                                         cudaStream_t, bool);                         \
+                                                         cudaStream_t, bool, int);                    \
+  template int tangent_resident_ctas<P, double, double>();                                              \
   template cudaError_t launch_tangent<P, float, double>(const HostElemData&, double, const double*,    \
                                                         double*, const float*, double*, PcgScalars*,   \
-                                                        cudaStream_t, bool);                          \
+                                                        cudaStream_t, bool, int);                     \
   template cudaError_t launch_tangent<P, float, float>(const HostElemData&, double, const float*,      \
                                                        float*, const float*, double*, PcgScalars*,     \
-                                                       cudaStream_t, bool);                           \
+                                                       cudaStream_t, bool, int);                      \
+  template int tangent_resident_ctas<P, float, float>();                                                \
   template cudaError_t launch_diag<P, double>(const HostElemData&, double, const double*, double*,     \
                                               cudaStream_t);                                          \
   template cudaError_t launch_diag<P, float>(const HostElemData&, double, const float*, float*,        \

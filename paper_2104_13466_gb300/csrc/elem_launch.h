@@ -106,9 +106,14 @@ cudaError_t launch_cond_columns(const HostElemData& h, double b1, const double* 
 template <int P>
 cudaError_t launch_residual(const HostElemData& h, double b1, const double* u, double* y, double* st64,
                             float* st32, int* err, cudaStream_t s);
+// grid > 0 (and below the element count): that many CTAs, each serving every
+// grid-th element, with one step-length partial per CTA; else one CTA per element.
 template <int P, typename T, typename TV>
 cudaError_t launch_tangent(const HostElemData& h, double b1, const TV* x, TV* y, const T* st,
-                           double* partial, PcgScalars* scal, cudaStream_t s, bool defer = false);
+                           double* partial, PcgScalars* scal, cudaStream_t s, bool defer = false, int grid = 0);
+// Resident CTAs per SM of the fixed-grid tangent kernel (0 on error).
+template <int P, typename T, typename TV>
+int tangent_resident_ctas();
 template <int P, typename T>
 cudaError_t launch_diag(const HostElemData& h, double b1, const T* st, T* y, cudaStream_t s);
 template <int P>

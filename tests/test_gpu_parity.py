@@ -168,6 +168,33 @@ def test_pcg_mixed_reaches_float32_tolerance():
     assert np.linalg.norm(r) < 1e-4 * np.linalg.norm(bm)
 
 
+@pytest.mark.parametrize("grid", [-1, 7])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pcg_with_a_fixed_tangent_grid(prec, grid):
+    # the tangent launch with fewer CTAs than elements (each CTA serving every
+    # grid-th element, one step-length partial per CTA) solves the same
+    # system as one CTA per element: against the dense direct solve, with the
+    # same iteration count up to the last few (summation order)
+    s = _sdme()
+    ctx, disc = _pair(elems=(3, 2, 2), lengths=(1.3, 0.7, 0.9), clamp={"xmin": (0, 1, 2), "zmax": (2,)}, P=4,
+                      kind="sdme_h", prec=s.MIXED_FP32 if prec else 0)
+    u = _u(disc, 61)
+    u[disc.mask] = 0.0
+    b = random_vector(disc.mesh.ndof, 62)
+    b1, rtol = 300.0, (1e-6 if prec else 1e-12)
+    x0 = torch.zeros(ctx.ndof, dtype=torch.float64, device="cuda")
+    its0, _ = ctx.pcg_solve(_dev(u), b1, _dev(b), x0, rtol=rtol, maxit=5000)
+    used = ctx.set_tangent_grid(grid)
+    assert 0 < used < disc.mesh.nelem or grid == -1
+    x = torch.zeros_like(x0)
+    its, rel = ctx.pcg_solve(_dev(u), b1, _dev(b), x, rtol=rtol, maxit=5000)
+    assert rel <= rtol and abs(its - its0) <= 2
+    bm = np.where(disc.mask, 0.0, b)
+    x_dir = solvers.dense_solve(disc.tangent_matrix(u, b1), bm)
+    assert _relerr(_host(x), x_dir) < (1e-4 if prec else 1e-9)
+    assert ctx.set_tangent_grid(0) == 0
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_pcg_above_the_deferred_size(prec):
     # 9,216 elements: above the size up to which the PCG update sums the

@@ -15,7 +15,7 @@ LIB = os.path.join(ROOT, "paper_2104_13466_gb300", "libsdme.so")
 
 def _declared():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:sdme_status|const char\*)\s+(sdme_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:sdme_status|const char\*|int)\s+(sdme_\w+)\s*\(", text, re.M)))
 
 
 @pytest.fixture(scope="module")
