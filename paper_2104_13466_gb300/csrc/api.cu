@@ -285,7 +285,7 @@ sdme_status pcg_chunk(sdme_ctx* ctx, double b1, int op, bool tim, TV* r, TV* p, 
                                       tim ? ctx->ev[2 * j + 1] : nullptr, defer, tgrid)));
     }
     constexpr int vi = sizeof(TV) == 4 ? 1 : 0;
-    k_pcg_update<TV><<<ctx->upd_blocks[vi], kVecThreads, 0, ctx->stream>>>(
+    k_pcg_update<TV><<<ctx->upd_blocks[vi], kUpdThreads, 0, ctx->stream>>>(
         ctx->ndof, r, q, dinv, ctx->scal, ctx->partial + ctx->upart_off, defer ? ctx->partial : nullptr, nparts);
     k_pcg_direction<TV><<<ctx->dir_blocks[vi], kVecThreads, 0, ctx->stream>>>(ctx->ndof, r, dinv, p, xh, xl,
                                                                              ctx->scal);
@@ -951,13 +951,14 @@ sdme_status sdme_create(sdme_ctx** out, const sdme_mesh_desc* mesh, const sdme_m
     int dev = 0, sms = 0;
     ok = cudaGetDevice(&dev) == cudaSuccess &&
          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
-    auto wave = [&](auto kernel, int* out) {
+    auto wave = [&](auto kernel, int* out, int threads = kVecThreads) {
       int per_sm = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kVecThreads, 0) != cudaSuccess) return false;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess) return false;
       *out = std::max(1, std::min(kVecBlocks, per_sm * sms));
       return true;
     };
-    ok = ok && wave(k_pcg_update<double>, &ctx->upd_blocks[0]) && wave(k_pcg_update<float>, &ctx->upd_blocks[1]) &&
+    ok = ok && wave(k_pcg_update<double>, &ctx->upd_blocks[0], kUpdThreads) &&
+         wave(k_pcg_update<float>, &ctx->upd_blocks[1], kUpdThreads) &&
          wave(k_pcg_direction<double>, &ctx->dir_blocks[0]) && wave(k_pcg_direction<float>, &ctx->dir_blocks[1]);
   }
   if (ok && basis->kind == SDME_NODAL_LUMPED) ok = build_lumped_mass(ctx) == SDME_OK;

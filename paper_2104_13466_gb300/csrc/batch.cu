@@ -123,6 +123,8 @@ struct sdme_batch {
   double persist_b1 = -1.0;   // b1 of the uploaded per-problem table
   PersistItem* items = nullptr;
   int* nitems = nullptr;
+  PersistItem* items_h = nullptr;   // pinned staging of the item list (its count follows the items)
+  int persist_grid_cache[512] = {}; // resident-CTA grid per set of running orders (bit P-1 per order)
   int* queue = nullptr;
   unsigned char* pprobs = nullptr;
 };
@@ -151,7 +153,7 @@ void batch_free(sdme_batch* b) {
                  b->d32, b->x32, b->un, b->ahat, b->mhat, b->y, b->psi, b->du, b->loc};
   for (void* p : dev)
     if (p) cudaFree(p);
-  void* host[] = {b->scal_h, b->dnorm_h, b->err_h, b->active_h};
+  void* host[] = {b->scal_h, b->dnorm_h, b->err_h, b->active_h, b->items_h};
   for (void* p : host)
     if (p) cudaFreeHost(p);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
@@ -256,10 +258,14 @@ sdme_status b_persist_items(sdme_batch* b, const std::vector<int>* run, double b
   b->persist_items_n = n;
   for (int P = 0; P <= 8; ++P) b->persist_run_orders[P] = 0;
   for (const PersistItem& it : items) b->persist_run_orders[it.P] = 1;
+  // staged in pinned memory (the caller reads the PCG status, a
+  // synchronisation, before it stages the next list), count after the items
+  std::memcpy(b->items_h, items.data(), sizeof(PersistItem) * n);
+  std::memcpy(reinterpret_cast<int*>(b->items_h + n), &n, sizeof(int));
   B_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream));
   if (n > 0)
-    B_CUDA(cudaMemcpyAsync(b->items, items.data(), sizeof(PersistItem) * n, cudaMemcpyHostToDevice, b->stream));
-  B_CUDA(cudaMemcpyAsync(b->nitems, &n, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    B_CUDA(cudaMemcpyAsync(b->items, b->items_h, sizeof(PersistItem) * n, cudaMemcpyHostToDevice, b->stream));
+  B_CUDA(cudaMemcpyAsync(b->nitems, b->items_h + n, sizeof(int), cudaMemcpyHostToDevice, b->stream));
   if (b->persist_b1 != b1) {
     std::vector<HostPersistProb> hp(b->nprob);
     for (int i = 0; i < b->nprob; ++i) {
@@ -276,9 +282,9 @@ sdme_status b_persist_items(sdme_batch* b, const std::vector<int>* run, double b
     else persist_probs_image<double>(hp, b1, img);
     B_CUDA(cudaMemcpyAsync(b->pprobs, img.data(), img.size(), cudaMemcpyHostToDevice, b->stream));
     b->persist_b1 = b1;
+    // the pageable table must stay valid until its copy has run
+    B_CUDA(cudaStreamSynchronize(b->stream));
   }
-  // the pageable sources must stay valid until the copies have run
-  B_CUDA(cudaStreamSynchronize(b->stream));
   return SDME_OK;
 }
 
@@ -297,6 +303,12 @@ sdme_status b_persist_launch(sdme_batch* b, const TV* x, TV* y, double* partial,
 }
 
 sdme_status b_persist_grid(sdme_batch* b) {
+  int mask = 0;
+  for (int P = 1; P <= 8; ++P) mask |= b->persist_run_orders[P] ? (1 << (P - 1)) : 0;
+  if (b->persist_grid_cache[mask] > 0) {
+    b->persist_grid = b->persist_grid_cache[mask];
+    return SDME_OK;
+  }
   const HostPersist hp = b_persist_desc(b);
   const int occ = b->prec == SDME_MIXED_FP32 ? persist_occupancy<float, float>(hp)
                                              : persist_occupancy<double, double>(hp);
@@ -305,6 +317,7 @@ sdme_status b_persist_grid(sdme_batch* b) {
   B_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (occ < 1) return SDME_ECUDA;
   b->persist_grid = occ * sms;
+  b->persist_grid_cache[mask] = b->persist_grid;
   return SDME_OK;
 }
 
@@ -634,6 +647,7 @@ sdme_status sdme_batch_create(sdme_batch** out, const sdme_problem* probs, int n
   ok = ok && dalloc(&b->un, nt) == cudaSuccess && dalloc(&b->ahat, nt) == cudaSuccess &&
        dalloc(&b->mhat, nt) == cudaSuccess && dalloc(&b->y, nt) == cudaSuccess &&
        dalloc(&b->psi, nt) == cudaSuccess && dalloc(&b->du, nt) == cudaSuccess;
+  ok = ok && cudaMallocHost((void**)&b->items_h, sizeof(PersistItem) * ((size_t)b->nelem_total + 1)) == cudaSuccess;
   ok = ok && dalloc(&b->items, (size_t)b->nelem_total) == cudaSuccess && dalloc(&b->nitems, 1) == cudaSuccess &&
        dalloc(&b->queue, 1) == cudaSuccess &&
        dalloc(&b->pprobs, np * (prec == SDME_MIXED_FP32 ? persist_prob_bytes<float>()
@@ -891,8 +905,10 @@ sdme_status sdme_batch_set_persistent(sdme_batch* b, int mode, const int* kper) 
       const int nt = (3 * (P + 2) * (P + 2) + 31) / 32 * 32;
       if (kper[P] < 1 || kper[P] > std::min(kPersistMaxTile, 320 / nt)) return SDME_EINVAL;
     }
-  if (kper)
+  if (kper) {
     for (int P = 1; P <= kMaxP; ++P) b->kper[P] = kper[P];
+    std::memset(b->persist_grid_cache, 0, sizeof(b->persist_grid_cache));
+  }
   b->persist_mode = mode;
   b->persist_on = mode == 1;
   if (b->gexec) {
@@ -1005,6 +1021,7 @@ sdme_status sdme_batch_tune(sdme_batch* b, int reps, int ngroups_max, int* ngrou
       int bestk = 1;
       for (int k = 1; k <= kmax && result == SDME_OK; ++k) {
         b->kper[g.P] = k;
+        std::memset(b->persist_grid_cache, 0, sizeof(b->persist_grid_cache));
         float t = 0.f;
         result = b_persist_items(b, nullptr, 0.0, g.P);
         if (result == SDME_OK) result = b_persist_grid(b);
@@ -1017,6 +1034,7 @@ sdme_status sdme_batch_tune(sdme_batch* b, int reps, int ngroups_max, int* ngrou
       b->kper[g.P] = bestk;
       b->persist_order_ms[g.P] = best;
     }
+    std::memset(b->persist_grid_cache, 0, sizeof(b->persist_grid_cache));
     if (result == SDME_OK) result = b_persist_items(b, nullptr, 0.0);
     if (result == SDME_OK) result = b_persist_grid(b);
     if (result == SDME_OK) result = time_persist(&b->persist_ms);

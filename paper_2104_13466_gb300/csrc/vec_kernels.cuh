@@ -240,8 +240,12 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_xout(int64_t n, const TV* _
     out[g] = xl ? (double)xh[g] + (double)xl[g] : (double)xh[g];
 }
 
+// Block size of the PCG update: 1024 threads, so that the CTAs that each
+// sum the operator's per-element partials (the step length) are few.
+constexpr int kUpdThreads = 1024;
+
 template <typename TV>
-__global__ void __launch_bounds__(kVecThreads) k_pcg_update(int64_t n, TV* __restrict__ r, TV* __restrict__ q,
+__global__ void __launch_bounds__(kUpdThreads) k_pcg_update(int64_t n, TV* __restrict__ r, TV* __restrict__ q,
                                                             const TV* __restrict__ dinv, PcgScalars* scal,
                                                             double* __restrict__ partial,
                                                             const double* __restrict__ dot_partial = nullptr,
