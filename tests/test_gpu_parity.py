@@ -174,7 +174,8 @@ def test_pcg_with_a_fixed_tangent_grid(prec, grid):
     # the tangent launch with fewer CTAs than elements (each CTA serving every
     # grid-th element, one step-length partial per CTA) solves the same
     # system as one CTA per element: against the dense direct solve, with the
-    # same iteration count up to the last few (summation order)
+    # same iteration count up to the last few (summation order; the float32
+    # recurrence with its float64 restarts drifts by a few per cent)
     s = _sdme()
     ctx, disc = _pair(elems=(3, 2, 2), lengths=(1.3, 0.7, 0.9), clamp={"xmin": (0, 1, 2), "zmax": (2,)}, P=4,
                       kind="sdme_h", prec=s.MIXED_FP32 if prec else 0)
@@ -188,7 +189,7 @@ def test_pcg_with_a_fixed_tangent_grid(prec, grid):
     assert 0 < used < disc.mesh.nelem or grid == -1
     x = torch.zeros_like(x0)
     its, rel = ctx.pcg_solve(_dev(u), b1, _dev(b), x, rtol=rtol, maxit=5000)
-    assert rel <= rtol and abs(its - its0) <= 2
+    assert rel <= rtol and abs(its - its0) <= (max(2, its0 // 20) if prec else 2)
     bm = np.where(disc.mask, 0.0, b)
     x_dir = solvers.dense_solve(disc.tangent_matrix(u, b1), bm)
     assert _relerr(_host(x), x_dir) < (1e-4 if prec else 1e-9)
