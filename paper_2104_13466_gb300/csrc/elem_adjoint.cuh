@@ -25,7 +25,7 @@ vjp_kernel(const __grid_constant__ ElemParams<double, P> prm, const double* __re
            unsigned int* counter, double* __restrict__ out) {
   using T = double;
   using G = Geo<P>;
-  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
+  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, FQ = G::FQ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   T* X = sm + 3 * FQ;
@@ -44,7 +44,7 @@ vjp_kernel(const __grid_constant__ ElemParams<double, P> prm, const double* __re
   T gmu = T(0), glam = T(0);
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
-    const int so = (qz * Q + qy) * XQ + qx;
+    const int so = G::pt(qx, qy, qz);
     T H[3][3], dW[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)

@@ -343,18 +343,34 @@ __device__ __forceinline__ T wprod(const T* W, int q, int Q) {
 // Shared-memory geometry of the element kernels for order P.  Arrays are
 // [component][z][y][x] with the x extent padded to an odd pitch so that
 // threads walking consecutive lines hit distinct banks.
+//   X   [3][n][n][XN]  element coefficients (gather / scatter layout)
+//   A1  [3][n][n][XQ]  after the x-stage, component stride SA1
+//   A2  [3][n][Q][XQ]  after the y-stage, z-slab pitch SP2, component stride SA2
+//   Q^3 fields [3][Q][Q][XQ], z-slab pitch SPQ, component stride FQ
+// SLAB (P = 8: ten warps, one per Gauss line of a direction): the y- and
+// z-line stages give each warp one slab of lines across the three
+// components, and the pitches are padded (SPQ = SP2 = Q XQ + 1, SA2 to
+// 10 mod 32, FQ = 22 mod 32) so that every warp access of every stage and
+// of the pointwise walk over the padded slots falls in 32 distinct banks.
 template <int P>
 struct Geo {
   static constexpr int n = P + 1, Q = P + 2;
   static constexpr int XQ = Q | 1;             // pitch of an x extent Q
   static constexpr int XN = n | 1;             // pitch of an x extent n
-  static constexpr int FQ = Q * Q * XQ;        // one component of a Q^3 field
+  static constexpr int NT = (3 * Q * Q + 31) / 32 * 32;   // one thread per (component, line)
+  static constexpr bool SLAB = (NT / 32 >= Q) && (3 * Q <= 32);
+  static constexpr int SPQ = Q * XQ + (SLAB ? 1 : 0);   // z-slab pitch of a Q^3 field
+  static constexpr int FQ = Q * SPQ;           // one component of a Q^3 field
   static constexpr int SX = n * n * XN;        // one component of X [n][n][n]
   static constexpr int SA1 = n * n * XQ;       // [n][n][Q]
-  static constexpr int SA2 = n * Q * XQ;       // [n][Q][Q]
-  static constexpr int NT = (3 * Q * Q + 31) / 32 * 32;   // one thread per (component, line)
+  static constexpr int SP2 = Q * XQ + (SLAB ? 1 : 0);   // z-slab pitch of A2
+  static constexpr int SA2 = SLAB ? (n * SP2 + 31 - Q) / 32 * 32 + Q : n * SP2;   // [n][Q][Q]
   static constexpr int WORDS = 12 * FQ;        // U, Gx, Gy, Gz
+  // offset of Gauss point (qx, qy, qz) within a Q^3 field
+  __host__ __device__ static constexpr int pt(int qx, int qy, int qz) { return qz * SPQ + qy * XQ + qx; }
 };
+static_assert(!Geo<8>::SLAB || (Geo<8>::SA2 % 32 == 10 && Geo<8>::FQ % 32 == 22 && 3 * Geo<8>::SA2 <= 3 * Geo<8>::FQ),
+              "P = 8 slab pitches");
 
 // Number of threads per CTA for order P.
 __host__ __device__ constexpr int elem_threads(int P) { return (3 * (P + 2) * (P + 2) + 31) / 32 * 32; }
@@ -362,6 +378,20 @@ __host__ __device__ constexpr int elem_threads(int P) { return (3 * (P + 2) * (P
 template <int P>
 constexpr int elem_smem_words() {
   return Geo<P>::WORDS;
+}
+
+// Thread-to-line maps of the stages.  Packed: thread t takes line t of the
+// stage's lines in [component][slow][fast] order.  Slab (Geo::SLAB): warp w
+// takes slab w of the lines and lane c * M + j the line (component c, index
+// j) of that slab, M lines per component.
+template <int P>
+__device__ __forceinline__ bool slab_line(int t, int M, int* c, int* slab, int* j) {
+  const int w = t >> 5, lane = t & 31;
+  if (w >= Geo<P>::Q || lane >= 3 * M) return false;
+  *c = lane / M;
+  *j = lane - *c * M;
+  *slab = w;
+  return true;
 }
 
 // Forward stages.  On entry X [3][n][n][XN] (in region 1) holds the element
@@ -378,7 +408,7 @@ constexpr int elem_smem_words() {
 template <typename T, int P, bool GRAD>
 __device__ __forceinline__ void forward_stages(const ElemTables<T, P>& tb, int pairs, T* sm, int t) {
   using G = Geo<P>;
-  constexpr int n = G::n, Q = G::Q, XQ = G::XQ, XN = G::XN, FQ = G::FQ;
+  constexpr int n = G::n, Q = G::Q, XQ = G::XQ, XN = G::XN, FQ = G::FQ, SPQ = G::SPQ, SP2 = G::SP2;
   T* U = sm;
   T* R1 = sm + 3 * FQ;
   T* R2 = sm + 6 * FQ;
@@ -395,49 +425,98 @@ __device__ __forceinline__ void forward_stages(const ElemTables<T, P>& tb, int p
     }
   }
   __syncthreads();
-  {  // F2: lines (c, r, qx)
-    constexpr int L = n * Q;
-    if (t < 3 * L) {
-      const int c = t / L, l = t - c * L, r = l / Q, qx = l - r * Q;
+  {  // F2: lines (c, r, qx); slab map: warp qx, lanes (c, r)
+    int c, r, qx;
+    bool on;
+    if constexpr (G::SLAB) {
+      on = slab_line<P>(t, n, &c, &qx, &r);
+    } else {
+      constexpr int L = n * Q;
+      on = t < 3 * L;
+      c = t / L;
+      const int l = t - c * L;
+      r = l / Q;
+      qx = l - r * Q;
+    }
+    if (on) {
       T in[n], out[Q];
       load_line(R2 + c * G::SA1 + r * n * XQ + qx, XQ, in);
       if (pairs) to_canonical(in);
       eo_interp(tb, in, out);
-      store_line(R1 + c * G::SA2 + r * Q * XQ + qx, XQ, out);
+      store_line(R1 + c * G::SA2 + r * SP2 + qx, XQ, out);
     }
   }
   __syncthreads();
-  {  // F3 (+ z-derivative): lines (c, qy, qx)
-    constexpr int L = Q * Q;
-    if (t < 3 * L) {
-      const int c = t / L, l = t - c * L, qy = l / Q, qx = l - qy * Q;
+  {  // F3 (+ z-derivative): lines (c, qy, qx); slab map: warp qy, lanes (c, qx)
+    int c, qy, qx;
+    bool on;
+    if constexpr (G::SLAB) {
+      on = slab_line<P>(t, Q, &c, &qy, &qx);
+    } else {
+      constexpr int L = Q * Q;
+      on = t < 3 * L;
+      c = t / L;
+      const int l = t - c * L;
+      qy = l / Q;
+      qx = l - qy * Q;
+    }
+    if (on) {
       T in[n], u[Q];
-      load_line(R1 + c * G::SA2 + qy * XQ + qx, Q * XQ, in);
+      load_line(R1 + c * G::SA2 + qy * XQ + qx, SP2, in);
       if (pairs) to_canonical(in);
       eo_interp(tb, in, u);
       const int o = c * FQ + qy * XQ + qx;
-      store_line(U + o, Q * XQ, u);
+      store_line(U + o, SPQ, u);
       if (GRAD) {
         T dz[Q];
         eo_deriv(tb, u, dz);
-        store_line(R3 + o, Q * XQ, dz);
+        store_line(R3 + o, SPQ, dz);
       }
     }
   }
   __syncthreads();
   if (GRAD) {
-    constexpr int L = Q * Q;
-    if (t < 3 * L) {
-      const int c = t / L, l = t - c * L, hi = l / Q, lo = l - hi * Q;
-      T v[Q], dv[Q];
-      // x-lines at (qz = hi, qy = lo)
-      load_line(U + c * FQ + l * XQ, 1, v);
-      eo_deriv(tb, v, dv);
-      store_line(R1 + c * FQ + l * XQ, 1, dv);
-      // y-lines at (qz = hi, qx = lo)
-      load_line(U + c * FQ + hi * Q * XQ + lo, XQ, v);
-      eo_deriv(tb, v, dv);
-      store_line(R2 + c * FQ + hi * Q * XQ + lo, XQ, dv);
+    {  // x-lines (c, qz, qy); slab map: warp qy, lanes (c, qz)
+      int c, qz, qy;
+      bool on;
+      if constexpr (G::SLAB) {
+        on = slab_line<P>(t, Q, &c, &qy, &qz);
+      } else {
+        constexpr int L = Q * Q;
+        on = t < 3 * L;
+        c = t / L;
+        const int l = t - c * L;
+        qz = l / Q;
+        qy = l - qz * Q;
+      }
+      if (on) {
+        T v[Q], dv[Q];
+        const int o = c * FQ + qz * SPQ + qy * XQ;
+        load_line(U + o, 1, v);
+        eo_deriv(tb, v, dv);
+        store_line(R1 + o, 1, dv);
+      }
+    }
+    {  // y-lines (c, qz, qx); slab map: warp qz, lanes (c, qx)
+      int c, qz, qx;
+      bool on;
+      if constexpr (G::SLAB) {
+        on = slab_line<P>(t, Q, &c, &qz, &qx);
+      } else {
+        constexpr int L = Q * Q;
+        on = t < 3 * L;
+        c = t / L;
+        const int l = t - c * L;
+        qz = l / Q;
+        qx = l - qz * Q;
+      }
+      if (on) {
+        T v[Q], dv[Q];
+        const int o = c * FQ + qz * SPQ + qx;
+        load_line(U + o, XQ, v);
+        eo_deriv(tb, v, dv);
+        store_line(R2 + o, XQ, dv);
+      }
     }
     __syncthreads();
   }
@@ -450,43 +529,81 @@ __device__ __forceinline__ void forward_stages(const ElemTables<T, P>& tb, int p
 //   T3        z-lines: w = U + DQ^T Gz, then B^T w -> A2' [3][n][Q][Q] (region 1)
 //   T2        y: A2' -> A1' [3][n][n][Q] (region 2)
 //   T1        x: A1' -> Y (region 1)
+// Each stage uses the thread-to-line map of its forward counterpart.
 template <typename T, int P, bool GRAD>
 __device__ __forceinline__ void transpose_stages(const ElemTables<T, P>& tb, int pairs, T* sm, int t) {
   using G = Geo<P>;
-  constexpr int n = G::n, Q = G::Q, XQ = G::XQ, XN = G::XN, FQ = G::FQ;
+  constexpr int n = G::n, Q = G::Q, XQ = G::XQ, XN = G::XN, FQ = G::FQ, SPQ = G::SPQ, SP2 = G::SP2;
   T* U = sm;
   T* R1 = sm + 3 * FQ;
   T* R2 = sm + 6 * FQ;
   T* R3 = sm + 9 * FQ;
   if (GRAD) {
-    constexpr int L = Q * Q;
-    if (t < 3 * L) {  // DTx: x-lines at (c, qz, qy)
-      const int c = t / L, l = t - c * L;
-      T g[Q], r[Q];
-      load_line(R1 + c * FQ + l * XQ, 1, g);
-      eo_deriv_t(tb, g, r);
-      add_line(U + c * FQ + l * XQ, 1, r);
+    {  // DTx: x-lines (c, qz, qy)
+      int c, qz, qy;
+      bool on;
+      if constexpr (G::SLAB) {
+        on = slab_line<P>(t, Q, &c, &qy, &qz);
+      } else {
+        constexpr int L = Q * Q;
+        on = t < 3 * L;
+        c = t / L;
+        const int l = t - c * L;
+        qz = l / Q;
+        qy = l - qz * Q;
+      }
+      if (on) {
+        T g[Q], r[Q];
+        const int o = c * FQ + qz * SPQ + qy * XQ;
+        load_line(R1 + o, 1, g);
+        eo_deriv_t(tb, g, r);
+        add_line(U + o, 1, r);
+      }
     }
     __syncthreads();
-    if (t < 3 * L) {  // DTy: y-lines at (c, qz, qx)
-      const int c = t / L, l = t - c * L, qz = l / Q, qx = l - qz * Q;
-      T g[Q], r[Q];
-      load_line(R2 + c * FQ + qz * Q * XQ + qx, XQ, g);
-      eo_deriv_t(tb, g, r);
-      add_line(U + c * FQ + qz * Q * XQ + qx, XQ, r);
+    {  // DTy: y-lines (c, qz, qx)
+      int c, qz, qx;
+      bool on;
+      if constexpr (G::SLAB) {
+        on = slab_line<P>(t, Q, &c, &qz, &qx);
+      } else {
+        constexpr int L = Q * Q;
+        on = t < 3 * L;
+        c = t / L;
+        const int l = t - c * L;
+        qz = l / Q;
+        qx = l - qz * Q;
+      }
+      if (on) {
+        T g[Q], r[Q];
+        const int o = c * FQ + qz * SPQ + qx;
+        load_line(R2 + o, XQ, g);
+        eo_deriv_t(tb, g, r);
+        add_line(U + o, XQ, r);
+      }
     }
     __syncthreads();
   }
-  {  // T3 (+ transposed z-derivative): z-lines at (c, qy, qx)
-    constexpr int L = Q * Q;
-    if (t < 3 * L) {
-      const int c = t / L, l = t - c * L, qy = l / Q, qx = l - qy * Q;
+  {  // T3 (+ transposed z-derivative): z-lines (c, qy, qx)
+    int c, qy, qx;
+    bool on;
+    if constexpr (G::SLAB) {
+      on = slab_line<P>(t, Q, &c, &qy, &qx);
+    } else {
+      constexpr int L = Q * Q;
+      on = t < 3 * L;
+      c = t / L;
+      const int l = t - c * L;
+      qy = l / Q;
+      qx = l - qy * Q;
+    }
+    if (on) {
       const int o = c * FQ + qy * XQ + qx;
       T w[Q];
-      load_line(U + o, Q * XQ, w);
+      load_line(U + o, SPQ, w);
       if (GRAD) {
         T g[Q], r[Q];
-        load_line(R3 + o, Q * XQ, g);
+        load_line(R3 + o, SPQ, g);
         eo_deriv_t(tb, g, r);
 #pragma unroll
         for (int a = 0; a < Q; ++a) w[a] += r[a];
@@ -494,16 +611,26 @@ __device__ __forceinline__ void transpose_stages(const ElemTables<T, P>& tb, int
       T out[n];
       eo_interp_t(tb, w, out);
       if (pairs) from_canonical(out);
-      store_line(R1 + c * G::SA2 + qy * XQ + qx, Q * XQ, out);
+      store_line(R1 + c * G::SA2 + qy * XQ + qx, SP2, out);
     }
   }
   __syncthreads();
   {  // T2: lines (c, r, qx)
-    constexpr int L = n * Q;
-    if (t < 3 * L) {
-      const int c = t / L, l = t - c * L, r = l / Q, qx = l - r * Q;
+    int c, r, qx;
+    bool on;
+    if constexpr (G::SLAB) {
+      on = slab_line<P>(t, n, &c, &qx, &r);
+    } else {
+      constexpr int L = n * Q;
+      on = t < 3 * L;
+      c = t / L;
+      const int l = t - c * L;
+      r = l / Q;
+      qx = l - r * Q;
+    }
+    if (on) {
       T in[Q], out[n];
-      load_line(R1 + c * G::SA2 + r * Q * XQ + qx, XQ, in);
+      load_line(R1 + c * G::SA2 + r * SP2 + qx, XQ, in);
       eo_interp_t(tb, in, out);
       if (pairs) from_canonical(out);
       store_line(R2 + c * G::SA1 + r * n * XQ + qx, XQ, out);
@@ -569,7 +696,7 @@ __device__ __forceinline__ void residual_body(const ElemTables<double, P>& tb, i
                                               int* __restrict__ err, double* sm) {
   using T = double;
   using G = Geo<P>;
-  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
+  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, FQ = G::FQ;
   T* X = sm + 3 * FQ;
   const ElemView<MeshParams<double>> view(m, P, e);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
@@ -583,7 +710,7 @@ __device__ __forceinline__ void residual_body(const ElemTables<double, P>& tb, i
   const T sc[3] = {m.s[0], m.s[1], m.s[2]};
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
-    const int so = (qz * Q + qy) * XQ + qx;
+    const int so = G::pt(qx, qy, qz);
     T F[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -691,7 +818,7 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
   if constexpr (!STIFF) {
     for (int q = t; q < Q3; q += NT) {
       const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
-      const int so = (qz * Q + qy) * XQ + qx;
+      const int so = G::pt(qx, qy, qz);
       const T mfac = m.b1 * m.rho * tb.W[qx] * tb.W[qy] * tb.W[qz] * m.detJ;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -710,9 +837,27 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
     const T mus2[3] = {m.mu * m.detJ * sc[0] * sc[0], m.mu * m.detJ * sc[1] * sc[1],
                        m.mu * m.detJ * sc[2] * sc[2]};
     const T b1rho = m.b1 * m.rho * m.detJ;
-    for (int q = t; q < Q3; q += NT) {
-      const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
-      const int so = (qz * Q + qy) * XQ + qx;
+    // slab layout: each warp pass takes three consecutive rows of Gauss
+    // points on its 30 lanes (consecutive state entries; their shared
+    // offsets span 32 consecutive words, so 30 distinct banks)
+    constexpr int WALK = G::SLAB ? (Q * Q + 2) / 3 * 32 : Q3;
+    for (int s = t; s < WALK; s += NT) {
+      int qx, qy, qz, q, so;
+      if constexpr (G::SLAB) {
+        const int lane = s & 31, r3 = lane / Q, row = 3 * (s >> 5) + r3;
+        qx = lane - r3 * Q;
+        if (lane >= 3 * Q || row >= Q * Q) continue;
+        qz = row / Q;
+        qy = row - qz * Q;
+        q = row * Q + qx;
+        so = G::pt(qx, qy, qz);
+      } else {
+        q = s;
+        qx = q % Q;
+        qy = (q / Q) % Q;
+        qz = q / (Q * Q);
+        so = G::pt(qx, qy, qz);
+      }
       T H[3][3], Gr[3][3];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -759,7 +904,7 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
   }
   for (int q = t; STIFF && sizeof(T) == 8 && q < Q3; q += NT) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
-    const int so = (qz * Q + qy) * XQ + qx;
+    const int so = G::pt(qx, qy, qz);
     T H[3][3], dF[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -947,7 +1092,7 @@ template <int P, typename T>
 __device__ __forceinline__ void mass_body(const ElemTables<T, P>& tb, int pairs, const MeshParams<T>& m, int e,
                                           const double* __restrict__ x, double* __restrict__ y, T* sm) {
   using G = Geo<P>;
-  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
+  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, FQ = G::FQ;
   T* X = sm + 3 * FQ;
   const ElemView<MeshParams<T>> view(m, P, e);
   for (int idx = threadIdx.x; idx < 3 * n3; idx += blockDim.x) {
@@ -960,7 +1105,7 @@ __device__ __forceinline__ void mass_body(const ElemTables<T, P>& tb, int pairs,
   forward_stages<T, P, false>(tb, pairs, sm, threadIdx.x);
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
-    const int so = (qz * Q + qy) * XQ + qx;
+    const int so = G::pt(qx, qy, qz);
     const T f = m.rho * tb.W[qx] * tb.W[qy] * tb.W[qz] * m.detJ;
 #pragma unroll
     for (int c = 0; c < 3; ++c) sm[c * FQ + so] *= f;
@@ -1140,7 +1285,7 @@ energy_kernel(const __grid_constant__ ElemParams<double, P> prm, const double* _
               double* __restrict__ partial, unsigned int* counter, double* out, int* __restrict__ err) {
   using T = double;
   using G = Geo<P>;
-  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
+  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, FQ = G::FQ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   T* X = sm + 3 * FQ;
@@ -1158,7 +1303,7 @@ energy_kernel(const __grid_constant__ ElemParams<double, P> prm, const double* _
   T acc = T(0);
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
-    const int so = (qz * Q + qy) * XQ + qx;
+    const int so = G::pt(qx, qy, qz);
     T F[3][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -1199,7 +1344,7 @@ body_load_kernel(const __grid_constant__ ElemParams<double, P> prm, const double
                  double* __restrict__ y) {
   using T = double;
   using G = Geo<P>;
-  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, XQ = G::XQ, FQ = G::FQ;
+  constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q, FQ = G::FQ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   T* X = sm + 3 * FQ;
@@ -1208,7 +1353,7 @@ body_load_kernel(const __grid_constant__ ElemParams<double, P> prm, const double
   const double* fe = fq + (int64_t)e * 3 * Q3;
   for (int q = threadIdx.x; q < Q3; q += blockDim.x) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
-    const int so = (qz * Q + qy) * XQ + qx;
+    const int so = G::pt(qx, qy, qz);
     const T wdet = prm.tab.W[qx] * prm.tab.W[qy] * prm.tab.W[qz] * prm.detJ;
 #pragma unroll
     for (int c = 0; c < 3; ++c) sm[c * FQ + so] = wdet * fe[c * Q3 + q];
