@@ -110,8 +110,11 @@ __global__ void __launch_bounds__(kVecThreads) k_axpy(int64_t n, double alpha, c
 
 //----------------------------------------------------------------------------
 // Jacobi PCG (CGD).  Vectors r, p, q, dinv in TV (dinv = 1 / diag).  The
-// solution x is float64 (TV = double) or, with float32 vectors, a float32
-// pair (hi, lo) holding hi + lo to about 48 bits: a float32 x would bound the
+// solution x is float64 (TV = double) or, with float32 vectors, either a
+// float32 pair (hi, lo) holding hi + lo to about 48 bits (xl given), or a
+// single float32 x (xl null) that the refined solves fold into a float64
+// solution at every refinement check, so that it only ever holds one
+// sweep's correction: a float32 x holding the whole solution would bound the
 // float64 residual b - A x at about eps32 |A| |x|, and float64 arithmetic
 // runs at a small fraction of the float32 rate on GB300.
 //   init:      r = scale*b (0 on constrained), x = 0, q = 0, p = z = dinv r,
@@ -222,10 +225,14 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_xfinal(int64_t n, const TV*
   const double alpha = scal->alpha;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
     if constexpr (sizeof(TV) == 4) {
-      float h = xh[g], l = xl[g];
-      pair_axpy(h, l, (float)alpha, p[g]);
-      xh[g] = h;
-      xl[g] = l;
+      if (xl) {
+        float h = xh[g], l = xl[g];
+        pair_axpy(h, l, (float)alpha, p[g]);
+        xh[g] = h;
+        xl[g] = l;
+      } else {
+        xh[g] += (float)alpha * p[g];
+      }
     } else {
       xh[g] += alpha * p[g];
     }
@@ -233,6 +240,25 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_xfinal(int64_t n, const TV*
 }
 
 // out = hi + lo in float64 (TV = float), or a copy of x (TV = double).
+// Refinement check of a single-x solve: x64 (+)= x in float64 (first: x64 =
+// x), then x = 0 for the next sweep's correction.
+template <typename TV>
+__global__ void __launch_bounds__(kVecThreads) k_pcg_xfold(int64_t n, TV* __restrict__ xh, double* __restrict__ x64,
+                                                           int first) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+    x64[g] = (first ? 0.0 : x64[g]) + (double)xh[g];
+    xh[g] = TV(0);
+  }
+}
+
+// out = x64 + x in float64 (a single-x solve that folded at least once).
+template <typename TV>
+__global__ void __launch_bounds__(kVecThreads) k_pcg_xout64(int64_t n, const TV* __restrict__ xh,
+                                                            const double* __restrict__ x64, double* __restrict__ out) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    out[g] = x64[g] + (double)xh[g];
+}
+
 template <typename TV>
 __global__ void __launch_bounds__(kVecThreads) k_pcg_xout(int64_t n, const TV* __restrict__ xh,
                                                           const TV* __restrict__ xl, double* __restrict__ out) {
@@ -376,10 +402,15 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_direction(int64_t n, const 
     V pv = reinterpret_cast<const V*>(p)[g];
     V hv = reinterpret_cast<const V*>(xh)[g];
     if constexpr (sizeof(TV) == 4) {
-      V lv = reinterpret_cast<const V*>(xl)[g];
+      if (xl) {
+        V lv = reinterpret_cast<const V*>(xl)[g];
 #pragma unroll
-      for (int i = 0; i < W; ++i) pair_axpy(lane(hv, i), lane(lv, i), alpha, lane(pv, i));
-      reinterpret_cast<V*>(xl)[g] = lv;
+        for (int i = 0; i < W; ++i) pair_axpy(lane(hv, i), lane(lv, i), alpha, lane(pv, i));
+        reinterpret_cast<V*>(xl)[g] = lv;
+      } else {
+#pragma unroll
+        for (int i = 0; i < W; ++i) lane(hv, i) += alpha * lane(pv, i);
+      }
     } else {
 #pragma unroll
       for (int i = 0; i < W; ++i) lane(hv, i) += alpha * lane(pv, i);
@@ -392,10 +423,14 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_direction(int64_t n, const 
   for (int64_t g = nv * W + t0; g < n; g += stride) {
     const TV pg = p[g];
     if constexpr (sizeof(TV) == 4) {
-      float h = xh[g], l = xl[g];
-      pair_axpy(h, l, alpha, pg);
-      xh[g] = h;
-      xl[g] = l;
+      if (xl) {
+        float h = xh[g], l = xl[g];
+        pair_axpy(h, l, alpha, pg);
+        xh[g] = h;
+        xl[g] = l;
+      } else {
+        xh[g] += alpha * pg;
+      }
     } else {
       xh[g] += alpha * pg;
     }
