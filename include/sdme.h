@@ -70,9 +70,13 @@ typedef enum {
                          Newton residual, PCG scalars and time-integrator state
                          in float64.  PCG dot products: float32 products (of
                          float32 vectors, summed four at a time) accumulated
-                         per thread and reduced in float64; the operator's
-                         p.(A p) from float32 Gauss-point terms accumulated in
-                         float64 */
+                         per thread in a compensated float32 (float-float,
+                         about 48-bit) sum and reduced across threads in
+                         float64; the operator's p.(A p) from float32
+                         Gauss-point terms accumulated the same way.  The
+                         refined tangent solves carry x as a float32
+                         correction folded into a float64 solution at every
+                         refinement check */
 } sdme_precision;
 
 enum { SDME_XMIN = 0, SDME_XMAX = 1, SDME_YMIN = 2, SDME_YMAX = 3, SDME_ZMIN = 4, SDME_ZMAX = 5 };

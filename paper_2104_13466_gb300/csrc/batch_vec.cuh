@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kVecThreads) kb_pcg_update(const BatchVecInfo*
   using V = typename Vec16<TV>::type;
   constexpr int W = Vec16<TV>::width;
   const TV alpha = (TV)sc->alpha;
-  double srz = 0.0, srr = 0.0;
+  typename AccOf<TV>::type srz, srr;
   TV *xs = x + b.off, *rs = r + b.off, *qs = q + b.off;
   const TV *ps = p + b.off, *ds = dinv + b.off;
   const int64_t n = b.mi.ndof, nv = n / W;
@@ -200,8 +200,8 @@ __global__ void __launch_bounds__(kVecThreads) kb_pcg_update(const BatchVecInfo*
       vrz += ri * (lane(dv, i) * ri);
       vrr += ri * ri;
     }
-    srz += (double)vrz;
-    srr += (double)vrr;
+    srz.add(vrz);
+    srr.add(vrr);
     reinterpret_cast<V*>(xs)[g] = xv;
     reinterpret_cast<V*>(rs)[g] = rv;
     reinterpret_cast<V*>(qs)[g] = V{};
@@ -212,10 +212,10 @@ __global__ void __launch_bounds__(kVecThreads) kb_pcg_update(const BatchVecInfo*
     const TV rv = rs[g] - alpha * qv;
     rs[g] = rv;
     qs[g] = TV(0);
-    srz += (double)(rv * (ds[g] * rv));
-    srr += (double)(rv * rv);
+    srz.add(rv * (ds[g] * rv));
+    srr.add(rv * rv);
   }
-  double a = srz, c = srr;
+  double a = srz.value(), c = srr.value();
   block_sum2(a, c);
   if (threadIdx.x == 0) {
     partial[2 * blockIdx.x] = a;

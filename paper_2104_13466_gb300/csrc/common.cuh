@@ -57,6 +57,38 @@ __device__ __forceinline__ bool dof_constrained(const MeshInfo& m, int64_t g) {
          ((iz == 0) && (m.clamp[4] & bit)) || ((iz == m.N[2] - 1) && (m.clamp[5] & bit));
 }
 
+// Per-thread partial sums of float32 terms.  A compensated (float-float)
+// accumulator: s + c carries the running sum to about 48 bits with float32
+// adds only (Knuth's TwoSum gives each addition's rounding error exactly,
+// collected in c), as accurate as a float64 accumulator of the same float32
+// terms; on GB300 the float64 pipe runs a small fraction of the float32 rate
+// and a float64 add per term kept the PCG update kernel float64-bound.
+struct FFSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    s = t;
+    c = __fadd_rn(c, err);
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Accumulator of TV terms: FFSum for float32, plain float64 for float64.
+template <typename TV>
+struct AccOf {
+  struct type {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ double value() const { return v; }
+  };
+};
+template <>
+struct AccOf<float> {
+  using type = FFSum;
+};
+
 // Sum over the CTA (float64); result valid in every thread.
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double red_[32];

@@ -806,7 +806,8 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
   // transposed stages are the exact adjoint of the forward ones, so the
   // element product equals the quadrature form
   // sum_q w_q (dF : dP + b1 rho |x(q)|^2), summed here at no memory cost
-  // (each Gauss point's term in float32, accumulated in float64).
+  // (each Gauss point's term in float32, accumulated per thread as a
+  // compensated float32 sum of about 48 bits and across threads in float64).
   // float64 (bound by the float64 pipe) returns 0; its caller re-reads x.
   constexpr bool QDOT = sizeof(T) == 4;
   double dotq = 0.0;
@@ -837,6 +838,7 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
     const T mus2[3] = {m.mu * m.detJ * sc[0] * sc[0], m.mu * m.detJ * sc[1] * sc[1],
                        m.mu * m.detJ * sc[2] * sc[2]};
     const T b1rho = m.b1 * m.rho * m.detJ;
+    FFSum dq;   // this thread's quadrature terms, compensated float32 sum
     // slab layout: each warp pass takes three consecutive rows of Gauss
     // points on its 30 lanes (consecutive state entries; their shared
     // offsets span 32 consecutive words, so 30 distinct banks)
@@ -899,8 +901,9 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
         sm[c * FQ + so] = u * mfac;
         if (QDOT) mq += u * u;
       }
-      if (QDOT) dotq += (double)(qf + mfac * mq);
+      if (QDOT) dq.add(qf + mfac * mq);
     }
+    dotq = dq.value();
   }
   for (int q = t; STIFF && sizeof(T) == 8 && q < Q3; q += NT) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);

@@ -130,8 +130,9 @@ __global__ void __launch_bounds__(kVecThreads) k_axpy(int64_t n, double alpha, c
 //              the iteration count kept): the refinement step of the float32
 //              solve.
 // Dot products: each product in TV (float32 products of float32 vectors are
-// summed four at a time, one 16-byte vector), accumulated per thread and
-// reduced across threads in float64.
+// summed four at a time, one 16-byte vector), accumulated per thread (float64,
+// or for float32 vectors in the update a compensated float32 sum of about 48
+// bits, FFSum) and reduced across threads in float64.
 //----------------------------------------------------------------------------
 template <typename TV>
 __global__ void __launch_bounds__(kVecThreads) k_pcg_init(MeshInfo mi, const double* __restrict__ b, double scale,
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_pcg_update(int64_t n, TV* __res
     alpha_d = scal->alpha;
   }
   const TV alpha = (TV)alpha_d;
-  double srz = 0.0, srr = 0.0;
+  typename AccOf<TV>::type srz, srr;
   auto body = [&](V& rv, V& qv, V& dv, int64_t g) {
     TV vrz = TV(0), vrr = TV(0);
 #pragma unroll
@@ -319,8 +320,8 @@ __global__ void __launch_bounds__(kUpdThreads) k_pcg_update(int64_t n, TV* __res
       vrz += ri * (lane(dv, i) * ri);
       vrr += ri * ri;
     }
-    srz += (double)vrz;
-    srr += (double)vrr;
+    srz.add(vrz);
+    srr.add(vrr);
     reinterpret_cast<V*>(r)[g] = rv;
     reinterpret_cast<V*>(q)[g] = V{};
   };
@@ -353,10 +354,10 @@ __global__ void __launch_bounds__(kUpdThreads) k_pcg_update(int64_t n, TV* __res
     const TV rv = r[g] - alpha * qv;
     r[g] = rv;
     q[g] = TV(0);
-    srz += (double)(rv * (dinv[g] * rv));
-    srr += (double)(rv * rv);
+    srz.add(rv * (dinv[g] * rv));
+    srr.add(rv * rv);
   }
-  double a = srz, c = srr;
+  double a = srz.value(), c = srr.value();
   block_sum2(a, c);
   if (threadIdx.x == 0) {
     partial[2 * blockIdx.x] = a;
