@@ -114,6 +114,9 @@ struct sdme_ctx {
   // restarts from the float64 residual per solve (0: off), and the outcome
   // of the last solve
   int refine_max = 8;
+  // PCG kernels of a chunk launched as programmatic dependents of their
+  // predecessors (each starts on the SMs its predecessor frees)
+  bool pdl = true;
   // CTAs of the PCG's tangent launch: 0 one per element, else that many
   // CTAs serving every tan_grid-th element (sdme_set_tangent_grid)
   int tan_grid = 0;
@@ -211,14 +214,16 @@ sdme_status sync_and_check(sdme_ctx* ctx) {
 
 template <typename T, typename TV>
 sdme_status tangent_launch(sdme_ctx* ctx, double b1, const TV* x, TV* y, double* partial, PcgScalars* scal,
-                           cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr, bool defer = false, int grid = 0) {
+                           cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr, bool defer = false, int grid = 0,
+                           bool pdl = false) {
   const HostElemData& h = ctx->h;
   const T* st;
   if constexpr (sizeof(T) == 8) st = ctx->st64;
   else st = ctx->st32;
   if (e0) SDME_CUDA(cudaEventRecord(e0, ctx->stream));
   SDME_CUDA(dispatch_P(h.P, [&](auto Pc) {
-    return launch_tangent<decltype(Pc)::value, T, TV>(h, b1, x, y, st, partial, scal, ctx->stream, defer, grid);
+    return launch_tangent<decltype(Pc)::value, T, TV>(h, b1, x, y, st, partial, scal, ctx->stream, defer, grid,
+                                                      pdl && !e0);
   }));
   if (e1) SDME_CUDA(cudaEventRecord(e1, ctx->stream));
   ctx->kernel_launches += 1;
@@ -283,14 +288,21 @@ sdme_status pcg_chunk(sdme_ctx* ctx, double b1, int op, bool tim, TV* r, TV* p, 
       }));
       ctx->kernel_launches += 1;
     } else {
+      // the operator of every iteration after the chunk's first overlaps the
+      // previous direction update's tail (programmatic dependent launch)
       SDME_TRY((tangent_launch<T, TV>(ctx, b1, p, q, ctx->partial, ctx->scal, tim ? ctx->ev[2 * j] : nullptr,
-                                      tim ? ctx->ev[2 * j + 1] : nullptr, defer, tgrid)));
+                                      tim ? ctx->ev[2 * j + 1] : nullptr, defer, tgrid, ctx->pdl && j > 0)));
     }
+    // update and direction start while their predecessor drains (their CTAs
+    // read the vectors the predecessor does not write before pdl_wait())
     constexpr int vi = sizeof(TV) == 4 ? 1 : 0;
-    k_pcg_update<TV><<<ctx->upd_blocks[vi], kUpdThreads, 0, ctx->stream>>>(
-        ctx->ndof, r, q, dinv, ctx->scal, ctx->partial + ctx->upart_off, defer ? ctx->partial : nullptr, nparts);
-    k_pcg_direction<TV><<<ctx->dir_blocks[vi], kVecThreads, 0, ctx->stream>>>(ctx->ndof, r, dinv, p, xh, xl,
-                                                                             ctx->scal);
+    const bool pdl_vec = ctx->pdl && !tim;
+    SDME_CUDA(launch_maybe_pdl(k_pcg_update<TV>, dim3(ctx->upd_blocks[vi]), dim3(kUpdThreads), 0, ctx->stream, pdl_vec,
+                               ctx->ndof, r, q, (const TV*)dinv, ctx->scal, ctx->partial + ctx->upart_off,
+                               (const double*)(defer ? ctx->partial : nullptr), nparts));
+    SDME_CUDA(launch_maybe_pdl(k_pcg_direction<TV>, dim3(ctx->dir_blocks[vi]), dim3(kVecThreads), 0, ctx->stream,
+                               ctx->pdl, ctx->ndof, (const TV*)r, (const TV*)dinv, p, xh, xl,
+                               (const PcgScalars*)ctx->scal));
   }
   SDME_CUDA(cudaGetLastError());
   return SDME_OK;

@@ -57,6 +57,16 @@ __device__ __forceinline__ bool dof_constrained(const MeshInfo& m, int64_t g) {
          ((iz == 0) && (m.clamp[4] & bit)) || ((iz == m.N[2] - 1) && (m.clamp[5] & bit));
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// the programmatic-serialization attribute may start while its predecessor
+// in the stream still runs: pdl_wait() returns once the predecessor grid has
+// completed and its memory operations are visible (at once for a normal
+// launch), and pdl_trigger() lets the successor start launching once every
+// CTA has issued it or exited.  A kernel reads nothing its predecessor writes
+// before pdl_wait().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Per-thread partial sums of float32 terms.  A compensated (float-float)
 // accumulator: s + c carries the running sum to about 48 bits with float32
 // adds only (Knuth's TwoSum gives each addition's rounding error exactly,

@@ -965,9 +965,6 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
   using G = Geo<P>;
   constexpr int n = P + 1, Q = P + 2, n3 = n * n * n, Q3 = Q * Q * Q;
   constexpr int NT = G::NT;  // == blockDim.x: compile-time strides let the loops batch their loads
-  // the solver's status word is read now and tested after the gather, so
-  // its latency overlaps the gather's loads (nothing is written before)
-  const int stat0 = scal ? *reinterpret_cast<volatile const int*>(&scal->status) : 0;
   if constexpr (STIFF) {
     // start pulling the element's linearisation state into L2 now; the
     // pointwise stage reads it after the gather and the forward stages
@@ -978,13 +975,20 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
   // fast path: an element off every clamped face with the offset table;
   // X is [3][n][n][n] unpadded for even P (odd n), so its offset is idx
   const bool fast = (G::XN == n) && loc != nullptr && !view.boundary;
-  if (fast) {
+  if (fast && threadIdx.x < 3 * n * n) {
     // the scatter's target lines, fetched into L2 while the element computes
-    if (threadIdx.x < 3 * n * n) {
-      const TV* yl = y + view.base + __ldg(loc + threadIdx.x * n);
-      prefetch_line_l2(yl);
-      prefetch_line_l2(yl + n - 1);
-    }
+    const TV* yl = y + view.base + __ldg(loc + threadIdx.x * n);
+    prefetch_line_l2(yl);
+    prefetch_line_l2(yl + n - 1);
+  }
+  // launched as the programmatic dependent of the PCG direction update, the
+  // element starts here, before x (its new direction) and the solver's
+  // status are final; the status is tested after the gather, so its latency
+  // overlaps the gather's loads (nothing is written before)
+  pdl_wait();
+  const int stat0 = scal ? *reinterpret_cast<volatile const int*>(&scal->status) : 0;
+  pdl_trigger();
+  if (fast) {
     const TV* xb = x + view.base;
 #pragma unroll
     for (int idx = threadIdx.x; idx < 3 * n3; idx += NT) X[idx] = (T)xb[__ldg(loc + idx)];

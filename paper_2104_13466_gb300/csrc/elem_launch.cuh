@@ -98,7 +98,7 @@ cudaError_t launch_residual(const HostElemData& h, double b1, const double* u, d
 
 template <int P, typename T, typename TV>
 cudaError_t launch_tangent(const HostElemData& h, double b1, const TV* x, TV* y, const T* st,
-                           double* partial, PcgScalars* scal, cudaStream_t s, bool defer, int grid) {
+                           double* partial, PcgScalars* scal, cudaStream_t s, bool defer, int grid, bool pdl) {
   if (h.dim == 2) return launch_quad_tangent<P, T, TV, true>(h, b1, x, y, st, partial, scal, s);
   static bool init = false;
   const size_t smem = sizeof(T) * elem_smem_words<P>();
@@ -113,7 +113,8 @@ cudaError_t launch_tangent(const HostElemData& h, double b1, const TV* x, TV* y,
     tangent_kernel_strided<P, T, TV><<<grid, elem_threads(P), smem, s>>>(prm, x, y, st, partial, scal, defer ? 1 : 0,
                                                                          h.nelem);
   else
-    tangent_kernel<P, T, TV><<<h.nelem, elem_threads(P), smem, s>>>(prm, x, y, st, partial, scal, defer ? 1 : 0);
+    return launch_maybe_pdl(tangent_kernel<P, T, TV, true>, dim3(h.nelem), dim3(elem_threads(P)), smem, s, pdl, prm,
+                            x, y, st, partial, scal, defer ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -220,14 +221,14 @@ cudaError_t launch_body_load(const HostElemData& h, const double* fq, double* y,
                                           float*, int*, cudaStream_t);                                \
   template cudaError_t launch_tangent<P, double, double>(const HostElemData&, double, const double*,   \
                                                          double*, const double*, double*, PcgScalars*, \
-                                                         cudaStream_t, bool, int);                    \
+                                                         cudaStream_t, bool, int, bool);                    \
   template int tangent_resident_ctas<P, double, double>();                                              \
   template cudaError_t launch_tangent<P, float, double>(const HostElemData&, double, const double*,    \
                                                         double*, const float*, double*, PcgScalars*,   \
-                                                        cudaStream_t, bool, int);                     \
+                                                        cudaStream_t, bool, int, bool);                     \
   template cudaError_t launch_tangent<P, float, float>(const HostElemData&, double, const float*,      \
                                                        float*, const float*, double*, PcgScalars*,     \
-                                                       cudaStream_t, bool, int);                      \
+                                                       cudaStream_t, bool, int, bool);                      \
   template int tangent_resident_ctas<P, float, float>();                                                \
   template cudaError_t launch_diag<P, double>(const HostElemData&, double, const double*, double*,     \
                                               cudaStream_t);                                          \

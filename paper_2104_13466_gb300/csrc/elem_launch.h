@@ -108,9 +108,31 @@ cudaError_t launch_residual(const HostElemData& h, double b1, const double* u, d
                             float* st32, int* err, cudaStream_t s);
 // grid > 0 (and below the element count): that many CTAs, each serving every
 // grid-th element, with one step-length partial per CTA; else one CTA per element.
+// pdl: launch as the programmatic dependent of the previous kernel in the
+// stream (one CTA per element only).
 template <int P, typename T, typename TV>
 cudaError_t launch_tangent(const HostElemData& h, double b1, const TV* x, TV* y, const T* st,
-                           double* partial, PcgScalars* scal, cudaStream_t s, bool defer = false, int grid = 0);
+                           double* partial, PcgScalars* scal, cudaStream_t s, bool defer = false, int grid = 0,
+                           bool pdl = false);
+
+// Kernel launch, optionally as the programmatic dependent of the previous
+// kernel in the stream (the kernel then calls pdl_wait() before it reads
+// anything that kernel writes).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_maybe_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                             Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 // Resident CTAs per SM of the fixed-grid tangent kernel (0 on error).
 template <int P, typename T, typename TV>
 int tangent_resident_ctas();

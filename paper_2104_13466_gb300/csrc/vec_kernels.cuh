@@ -197,6 +197,11 @@ struct Vec16<double> {
   static constexpr int width = 2;
 };
 
+// 16-byte load cached in L2 only (no stale L1 line of a vector rewritten by
+// an earlier launch)
+__device__ __forceinline__ float4 ldcg_vec(const float4* p) { return __ldcg(p); }
+__device__ __forceinline__ double2 ldcg_vec(const double2* p) { return __ldcg(p); }
+
 template <typename V>
 __device__ __forceinline__ auto& lane(V& v, int i) {
   return reinterpret_cast<typename std::remove_reference<decltype(v.x)>::type*>(&v)[i];
@@ -277,21 +282,26 @@ __global__ void __launch_bounds__(kUpdThreads) k_pcg_update(int64_t n, TV* __res
                                                             double* __restrict__ partial,
                                                             const double* __restrict__ dot_partial = nullptr,
                                                             int nparts = 0) {
-  if (scal->status != kPcgRunning) return;
   using V = typename Vec16<TV>::type;
   constexpr int W = Vec16<TV>::width;
   const int64_t nv = n / W;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   // the first chunk's loads do not depend on the step length: issue them
-  // before it is summed so that their latency overlaps the sum
+  // before it is summed so that their latency overlaps the sum.  r and 1/d
+  // are not written by the operator launch this one may overlap (launched
+  // as its programmatic dependent): they are read before pdl_wait(), through
+  // L2; q after it
   V r0, q0, d0;
   const bool first = t0 < nv;
   if (first) {
-    r0 = reinterpret_cast<const V*>(r)[t0];
-    q0 = reinterpret_cast<const V*>(q)[t0];
-    d0 = reinterpret_cast<const V*>(dinv)[t0];
+    r0 = ldcg_vec(reinterpret_cast<const V*>(r) + t0);
+    d0 = ldcg_vec(reinterpret_cast<const V*>(dinv) + t0);
   }
+  pdl_wait();
+  if (scal->status != kPcgRunning) return;
+  pdl_trigger();
+  if (first) q0 = reinterpret_cast<const V*>(q)[t0];
   double alpha_d;
   if (dot_partial) {
     // p . (A p) from the operator's per-element partials (which must not
@@ -388,20 +398,39 @@ __global__ void __launch_bounds__(kVecThreads) k_pcg_direction(int64_t n, const 
                                                                const TV* __restrict__ dinv, TV* __restrict__ p,
                                                                TV* __restrict__ xh, TV* __restrict__ xl,
                                                                const PcgScalars* scal) {
-  if (scal->status != kPcgRunning) return;
   using V = typename Vec16<TV>::type;
   constexpr int W = Vec16<TV>::width;
-  const TV beta = (TV)scal->beta;
-  const double alpha_d = scal->alpha;
-  const TV alpha = (TV)alpha_d;
   const int64_t nv = n / W;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // p, x and 1/d of the first chunk are not written by the update this
+  // launch may overlap (as its programmatic dependent): read them before
+  // pdl_wait(), through L2; r, the scalars and the status after it
+  V p0, h0, d0;
+  const bool first = t0 < nv;
+  if (first) {
+    p0 = ldcg_vec(reinterpret_cast<const V*>(p) + t0);
+    h0 = ldcg_vec(reinterpret_cast<const V*>(xh) + t0);
+    d0 = ldcg_vec(reinterpret_cast<const V*>(dinv) + t0);
+  }
+  pdl_wait();
+  if (scal->status != kPcgRunning) return;
+  pdl_trigger();
+  const TV beta = (TV)scal->beta;
+  const double alpha_d = scal->alpha;
+  const TV alpha = (TV)alpha_d;
   for (int64_t g = t0; g < nv; g += stride) {
     V rv = reinterpret_cast<const V*>(r)[g];
-    V dv = reinterpret_cast<const V*>(dinv)[g];
-    V pv = reinterpret_cast<const V*>(p)[g];
-    V hv = reinterpret_cast<const V*>(xh)[g];
+    V dv, pv, hv;
+    if (g == t0) {
+      dv = d0;
+      pv = p0;
+      hv = h0;
+    } else {
+      dv = reinterpret_cast<const V*>(dinv)[g];
+      pv = reinterpret_cast<const V*>(p)[g];
+      hv = reinterpret_cast<const V*>(xh)[g];
+    }
     if constexpr (sizeof(TV) == 4) {
       if (xl) {
         V lv = reinterpret_cast<const V*>(xl)[g];
