@@ -85,6 +85,16 @@ struct FFSum {
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// s + c += s2 + c2 (TwoSum of the leading words, the low words added):
+// commutative, so a butterfly reduction leaves the same pair in every lane.
+__device__ __forceinline__ void ff_merge(float& s, float& c, float s2, float c2) {
+  const float t = __fadd_rn(s, s2);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+  s = t;
+  c = __fadd_rn(__fadd_rn(c, c2), err);
+}
+
 // Accumulator of TV terms: FFSum for float32, plain float64 for float64.
 template <typename TV>
 struct AccOf {
@@ -136,6 +146,44 @@ __device__ __forceinline__ T block_sum_t(T v) {
   }
   __syncthreads();
   return out_t_;
+}
+
+// Two CTA sums of compensated float32 partials, in float64 in every thread:
+// the warps reduce their pairs with float32 adds (ff_merge), and only the
+// per-warp totals go through the float64 pipe.
+__device__ __forceinline__ void block_sum2_ff(const FFSum& a, const FFSum& b, double& oa, double& ob) {
+  __shared__ double fa_[32], fb_[32];
+  __shared__ double foa_, fob_;
+  float as = a.s, ac = a.c, bs = b.s, bc = b.c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float as2 = __shfl_xor_sync(0xffffffffu, as, o), ac2 = __shfl_xor_sync(0xffffffffu, ac, o);
+    const float bs2 = __shfl_xor_sync(0xffffffffu, bs, o), bc2 = __shfl_xor_sync(0xffffffffu, bc, o);
+    ff_merge(as, ac, as2, ac2);
+    ff_merge(bs, bc, bs2, bc2);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    fa_[threadIdx.x >> 5] = (double)as + (double)ac;
+    fb_[threadIdx.x >> 5] = (double)bs + (double)bc;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const bool ok = threadIdx.x < ((blockDim.x + 31) >> 5);
+    double x = ok ? fa_[threadIdx.x] : 0.0, y = ok ? fb_[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, o);
+      y += __shfl_xor_sync(0xffffffffu, y, o);
+    }
+    if (threadIdx.x == 0) {
+      foa_ = x;
+      fob_ = y;
+    }
+  }
+  __syncthreads();
+  oa = foa_;
+  ob = fob_;
 }
 
 // Two sums at once.

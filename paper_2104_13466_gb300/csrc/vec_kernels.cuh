@@ -307,15 +307,22 @@ __global__ void __launch_bounds__(kUpdThreads) k_pcg_update(int64_t n, TV* __res
     // p . (A p) from the operator's per-element partials (which must not
     // alias `partial`), summed by every CTA in the same fixed order so that
     // all CTAs hold the same step length; CTA 0 publishes it
+    // (one thread divides: a float64 division per thread of a 1024-thread
+    // CTA would hold the float64 pipe for microseconds)
     const double pq = ordered_sum_prev(dot_partial, nparts);
-    alpha_d = scal->rz / pq;
-    const bool bad = !(pq > 0.0) || !isfinite(alpha_d);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      scal->pq = pq;
-      scal->alpha = alpha_d;
-      if (bad) scal->status = kPcgBreakdown;
+    __shared__ double s_alpha;
+    if (threadIdx.x == 0) {
+      const double al = scal->rz / pq;
+      s_alpha = (!(pq > 0.0) || !isfinite(al)) ? -1.0 : al;
+      if (blockIdx.x == 0) {
+        scal->pq = pq;
+        scal->alpha = al;
+        if (s_alpha < 0.0) scal->status = kPcgBreakdown;
+      }
     }
-    if (bad) return;  // every CTA takes the same branch; none reaches the counter
+    __syncthreads();
+    alpha_d = s_alpha;
+    if (alpha_d < 0.0) return;  // every CTA takes the same branch; none reaches the counter
   } else {
     alpha_d = scal->alpha;
   }
@@ -367,8 +374,14 @@ __global__ void __launch_bounds__(kUpdThreads) k_pcg_update(int64_t n, TV* __res
     srz.add(rv * (dinv[g] * rv));
     srr.add(rv * rv);
   }
-  double a = srz.value(), c = srr.value();
-  block_sum2(a, c);
+  double a, c;
+  if constexpr (sizeof(TV) == 4) {
+    block_sum2_ff(srz, srr, a, c);
+  } else {
+    a = srz.value();
+    c = srr.value();
+    block_sum2(a, c);
+  }
   if (threadIdx.x == 0) {
     partial[2 * blockIdx.x] = a;
     partial[2 * blockIdx.x + 1] = c;
