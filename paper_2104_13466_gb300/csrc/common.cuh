@@ -186,6 +186,30 @@ __device__ __forceinline__ void block_sum2_ff(const FFSum& a, const FFSum& b, do
   ob = fob_;
 }
 
+// CTA sum of compensated float32 partials in float64, valid in every thread
+// (as block_sum2_ff, one value).
+__device__ __forceinline__ double block_sum_ff(const FFSum& a) {
+  __shared__ double fr_[32];
+  __shared__ double fo_;
+  float as = a.s, ac = a.c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float as2 = __shfl_xor_sync(0xffffffffu, as, o), ac2 = __shfl_xor_sync(0xffffffffu, ac, o);
+    ff_merge(as, ac, as2, ac2);
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) fr_[threadIdx.x >> 5] = (double)as + (double)ac;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double x = (threadIdx.x < ((blockDim.x + 31) >> 5)) ? fr_[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (threadIdx.x == 0) fo_ = x;
+  }
+  __syncthreads();
+  return fo_;
+}
+
 // Two sums at once.
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
   __shared__ double ra_[32], rb_[32];

@@ -800,7 +800,8 @@ constexpr int tangent_min_blocks() {
 // when a CTA serves one element).
 template <int P, typename T, bool STIFF>
 __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int pairs, const MeshParams<T>& m,
-                                               int e, const T* __restrict__ st, T* sm, int t) {
+                                               int e, const T* __restrict__ st, T* sm, int t,
+                                               FFSum* ffdot = nullptr) {
   using G = Geo<P>;
   // float32: returns this thread's share of x_e . (K_e x_e).  The
   // transposed stages are the exact adjoint of the forward ones, so the
@@ -817,16 +818,23 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
   const T sc[3] = {m.s[0], m.s[1], m.s[2]};
   const T* ste = st + (int64_t)e * kStateFields * Q3;
   if constexpr (!STIFF) {
+    FFSum dq;
     for (int q = t; q < Q3; q += NT) {
       const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
       const int so = G::pt(qx, qy, qz);
       const T mfac = m.b1 * m.rho * tb.W[qx] * tb.W[qy] * tb.W[qz] * m.detJ;
+      T mq = T(0);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const T u = sm[c * FQ + so];
         sm[c * FQ + so] = u * mfac;
-        if (QDOT) dotq += (double)(mfac * u * u);
+        mq += u * u;
       }
+      if (QDOT) dq.add((float)(mfac * mq));
+    }
+    if (QDOT) {
+      if (ffdot) *ffdot = dq;
+      else dotq = dq.value();
     }
   }
   if constexpr (STIFF && sizeof(T) == 4) {
@@ -903,7 +911,8 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
       }
       if (QDOT) dq.add(qf + mfac * mq);
     }
-    dotq = dq.value();
+    if (ffdot) *ffdot = dq;
+    else dotq = dq.value();
   }
   for (int q = t; STIFF && sizeof(T) == 8 && q < Q3; q += NT) {
     const int qx = q % Q, qy = (q / Q) % Q, qz = q / (Q * Q);
@@ -1003,7 +1012,10 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
   }
   __syncthreads();
   if (stat0 != 0) return;
-  double dotT = tangent_core<P, T, STIFF>(tb, pairs, m, e, st, sm, threadIdx.x);
+  // float32: the quadrature form's terms stay a compensated float32 pair per
+  // thread until the CTA sum (float64 only across the warps' totals)
+  FFSum ffdot;
+  double dotT = tangent_core<P, T, STIFF>(tb, pairs, m, e, st, sm, threadIdx.x, sizeof(T) == 4 ? &ffdot : nullptr);
   constexpr bool RELOAD = sizeof(T) == 8;  // float64: x_e . y_e from a second read of x
   if (fast) {
     const TV* xb = x + view.base;
@@ -1033,7 +1045,7 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
     // length (x_e is zero on constrained entries); float64 within the CTA
     // and across CTAs in a fixed order: by the last CTA to finish here, or
     // (defer) by every CTA of the following PCG update.
-    const double tot = block_sum(dotT);
+    const double tot = sizeof(T) == 4 ? block_sum_ff(ffdot) : block_sum(dotT);
     if (acc) {  // a CTA serving several elements sums them (see tangent_kernel_strided)
       if (threadIdx.x == 0) *acc += tot;
       return;
