@@ -1042,8 +1042,10 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
   }
   if (dot_partial) {
     // x_e . (K_e x_e) summed over elements gives x . (K x) for the PCG step
-    // length (x_e is zero on constrained entries); float64 within the CTA
-    // and across CTAs in a fixed order: by the last CTA to finish here, or
+    // length (x_e is zero on constrained entries); within the CTA as
+    // compensated float32 pairs over each warp and float64 across warps
+    // (float32 operator) or in float64 (float64 operator), and across CTAs
+    // in float64 in a fixed order: by the last CTA to finish here, or
     // (defer) by every CTA of the following PCG update.
     const double tot = sizeof(T) == 4 ? block_sum_ff(ffdot) : block_sum(dotT);
     if (acc) {  // a CTA serving several elements sums them (see tangent_kernel_strided)
