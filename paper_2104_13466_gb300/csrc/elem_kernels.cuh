@@ -116,6 +116,27 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
 }
 
+// L2 evict-first access policy (streamed data that must not displace the
+// PCG vectors from L2).
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float ld_ef(const float* a, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void prefetch_l2_ef(const void* p, size_t bytes, uint64_t pol) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  const uintptr_t lo = (a + 15) & ~uintptr_t(15), hi = (a + bytes) & ~uintptr_t(15);
+  if (hi > lo)
+    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(lo), "r"((unsigned)(hi - lo)),
+                 "l"(pol)
+                 : "memory");
+}
+
 // Hint that the cache line holding p be fetched into L2.
 __device__ __forceinline__ void prefetch_line_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
@@ -846,6 +867,7 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
     const T mus2[3] = {m.mu * m.detJ * sc[0] * sc[0], m.mu * m.detJ * sc[1] * sc[1],
                        m.mu * m.detJ * sc[2] * sc[2]};
     const T b1rho = m.b1 * m.rho * m.detJ;
+    const uint64_t pol = l2_evict_first();
     FFSum dq;   // this thread's quadrature terms, compensated float32 sum
     // slab layout: each warp pass takes three consecutive rows of Gauss
     // points on its 30 lanes (consecutive state entries; their shared
@@ -873,10 +895,10 @@ __device__ __forceinline__ double tangent_core(const ElemTables<T, P>& tb, int p
       for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          H[c][d] = ste[(c * 3 + d) * Q3 + q];
+          H[c][d] = ld_ef(ste + (c * 3 + d) * Q3 + q, pol);
           Gr[c][d] = sm[(3 + 3 * d + c) * FQ + so];
         }
-      const T cst = ste[9 * Q3 + q];
+      const T cst = ld_ef(ste + 9 * Q3 + q, pol);
       T tr = T(0);
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -977,7 +999,12 @@ __device__ __forceinline__ void tangent_body(const ElemTables<T, P>& tb, int pai
   if constexpr (STIFF) {
     // start pulling the element's linearisation state into L2 now; the
     // pointwise stage reads it after the gather and the forward stages
-    if (threadIdx.x == 0) prefetch_l2(st + (int64_t)e * kStateFields * Q3, sizeof(T) * kStateFields * Q3);
+    if (threadIdx.x == 0) {
+      if constexpr (sizeof(T) == 4)
+        prefetch_l2_ef(st + (int64_t)e * kStateFields * Q3, sizeof(T) * kStateFields * Q3, l2_evict_first());
+      else
+        prefetch_l2(st + (int64_t)e * kStateFields * Q3, sizeof(T) * kStateFields * Q3);
+    }
   }
   T* X = sm + 3 * G::FQ;
   const ElemView<MeshParams<T>> view(m, P, e);
