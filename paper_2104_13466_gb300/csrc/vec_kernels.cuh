@@ -202,6 +202,22 @@ struct Vec16<double> {
 __device__ __forceinline__ float4 ldcg_vec(const float4* p) { return __ldcg(p); }
 __device__ __forceinline__ double2 ldcg_vec(const double2* p) { return __ldcg(p); }
 
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float4 ld_el(const float4* p, uint64_t pol) {
+  float4 v;
+  asm("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double2 ld_el(const double2* p, uint64_t) { return *p; }
+__device__ __forceinline__ void st_el(float4* p, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_el(double2* p, double2 v, uint64_t) { *p = v; }
+
 template <typename V>
 __device__ __forceinline__ auto& lane(V& v, int i) {
   return reinterpret_cast<typename std::remove_reference<decltype(v.x)>::type*>(&v)[i];
@@ -328,6 +344,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_pcg_update(int64_t n, TV* __res
   }
   const TV alpha = (TV)alpha_d;
   typename AccOf<TV>::type srz, srr;
+  const uint64_t pol = l2_evict_last();   // r and 1/d kept in L2 for the direction update
   auto body = [&](V& rv, V& qv, V& dv, int64_t g) {
     TV vrz = TV(0), vrr = TV(0);
 #pragma unroll
@@ -339,7 +356,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_pcg_update(int64_t n, TV* __res
     }
     srz.add(vrz);
     srr.add(vrr);
-    reinterpret_cast<V*>(r)[g] = rv;
+    st_el(reinterpret_cast<V*>(r) + g, rv, pol);
     reinterpret_cast<V*>(q)[g] = V{};
   };
   int64_t g = t0;
@@ -355,7 +372,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_pcg_update(int64_t n, TV* __res
     for (int u = 0; u < 2; ++u) {
       rv[u] = reinterpret_cast<const V*>(r)[g + u * stride];
       qv[u] = reinterpret_cast<const V*>(q)[g + u * stride];
-      dv[u] = reinterpret_cast<const V*>(dinv)[g + u * stride];
+      dv[u] = ld_el(reinterpret_cast<const V*>(dinv) + g + u * stride, pol);
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u) body(rv[u], qv[u], dv[u], g + u * stride);
@@ -363,7 +380,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_pcg_update(int64_t n, TV* __res
   for (; g < nv; g += stride) {
     V rv = reinterpret_cast<const V*>(r)[g];
     V qv = reinterpret_cast<const V*>(q)[g];
-    V dv = reinterpret_cast<const V*>(dinv)[g];
+    V dv = ld_el(reinterpret_cast<const V*>(dinv) + g, pol);
     body(rv, qv, dv, g);
   }
   for (int64_t g = nv * W + t0; g < n; g += stride) {  // tail
