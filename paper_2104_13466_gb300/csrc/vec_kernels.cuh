@@ -202,6 +202,9 @@ struct Vec16<double> {
 __device__ __forceinline__ float4 ldcg_vec(const float4* p) { return __ldcg(p); }
 __device__ __forceinline__ double2 ldcg_vec(const double2* p) { return __ldcg(p); }
 
+// L2 evict-last access policy and 16-byte loads / stores under it (float32
+// vectors; the float64 overloads are plain accesses): vectors that the next
+// kernel reads again stay in L2 ahead of streamed data.
 __device__ __forceinline__ uint64_t l2_evict_last() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
